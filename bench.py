@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the truncated short-range P2P gravity on one GB300.
+
+Metric: pair interactions per second (G/s) of the FP32-table forward path,
+with the plain FP64 path timed beside it, and % of FP32 peak at the paper's
+51 flops per interaction (Section 5).  Workload: 128^3 particles, 60 % of the
+mass in 4000 NFW halos + 40 % uniform, periodic L = 500, N_PM = 128 (r_s =
+1.2 L/N_PM, r_c = 4.5 r_s), octree leaves <= 32 (seeded synthetic stand-in for
+the paper's cosmological initial conditions).
+
+A step is one forward evaluation over the whole particle set (kernel with the
+un-permute fused) with the leaf set resident on the device; the leaf build is
+host work reported separately and included in the end-to-end number.  Each
+timed step is bracketed by CUDA events on the launching stream; L2 is flushed
+(256 MB write) between steps.  `--gpus N` (torchrun) gives every rank its own
+box of the same workload (weak scaling, no collective on the data path).
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_INTERACTION = 51  # paper, Section 5
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="psr", choices=["psr", "reference"])
+    p.add_argument("--table-n", type=int, default=1024)
+    p.add_argument("--interp", default="linear", choices=["linear", "cubic"])
+    p.add_argument("--accum", default="fp64", choices=["fp64", "kahan"])
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-targets", type=int, default=100000,
+                   help="targets in the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--nside", type=int, default=128)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[4:8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def cpu_baseline(b, acc_gpu, n_targets, seed=2024):
+    """FP64 oracle on a bounded sample of targets (all sources), host cores."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    tg = np.sort(rng.choice(b.n, min(n_targets, b.n), replace=False))
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    ref, pairs, _ = oracle.forces(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, targets=tg, cells=True,
+                                  threads=threads)
+    dt = time.perf_counter() - t0
+    err = None
+    if acc_gpu is not None:
+        d = acc_gpu[tg] - ref
+        err = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+    return {"value": float(pairs.sum()) / dt / 1e9, "unit": "G pair-interactions/s",
+            "cores": threads, "kind": "oracle",
+            "sample": "%d random targets of the workload against all %d sources (within-cutoff "
+                      "pairs counted), cell-list FP64 brute force, %.1f s" % (tg.size, b.n, dt),
+            "seconds": dt, "pairs": int(pairs.sum())}, err, tg.size
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    b = synth.precision(nside=args.nside)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(b, None, max(1000, args.cpu_targets // 20))
+    for k in range(args.steps):
+        cb, _, _ = cpu_baseline(b, None, max(1000, args.cpu_targets // 20), seed=100 + k)
+        vals.append(cb)
+    pairs = sum(v["pairs"] for v in vals)
+    secs = sum(v["seconds"] for v in vals)
+    value = pairs / secs / 1e9
+    line = {"impl": "reference", "metric": "pair-interactions/s (FP64 CPU oracle)",
+            "value": value, "unit": "G pair-interactions/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(b, args),
+            "cpu_baseline": {"value": value, "unit": "G pair-interactions/s",
+                             "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": "each step: %d random targets against all sources"
+                                       % max(1000, args.cpu_targets // 20)},
+            "e2e": {"value": value, "unit": "G pair-interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(b, args):
+    return {"workload": "NFW-clustered %d^3, L=%g, N_PM=%d, 60%% mass in 4000 halos, "
+                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=32" % (args.nside, b.L, b.n_pm),
+            "n": b.n, "L": b.L, "r_s": b.r_s, "r_c": b.r_c, "max_leaf": 32,
+            "path": "FP32 pair math, T from a %d-interval %s table in shared memory, %s "
+                    "accumulation" % (args.table_n, args.interp, args.accum),
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def run_psr(args):
+    import numpy as np
+    import torch
+
+    import paper_2107_14008_gb300 as psr
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    b = synth.precision(seed=12346 + rank, nside=args.nside)
+    t0 = time.perf_counter()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
+    build_s = time.perf_counter() - t0
+    lv.upload(dev)
+    info = lv.info
+    opts = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=args.table_n,
+                       interp=psr.PSR_LINEAR if args.interp == "linear" else psr.PSR_CUBIC,
+                       accum=psr.PSR_ACC_FP64 if args.accum == "fp64" else psr.PSR_ACC_KAHAN32)
+    acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        lv.forces(opts, out=acc)
+    lv.check()
+    # within-cutoff pairs (untimed counting run)
+    lv.forces(psr.Options(precision=opts.precision, table_n=opts.table_n, interp=opts.interp,
+                          accum=opts.accum, count_pairs=True), out=acc)
+    within = lv.pair_count()
+    lv.forces(opts, out=acc)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            lv.forces(opts, out=acc)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = [a.elapsed_time(e) for a, e in evs]
+    total_ms = sum(ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    lv.check()
+    acc32 = acc.double().cpu().numpy()
+    evaluated = info.evaluated_pairs
+    value = world * evaluated * args.steps / (total_ms / 1e3) / 1e9
+    mean_ms = total_ms / args.steps
+
+    # FP64 path beside it
+    fp64 = None
+    if args.fp64_steps > 0:
+        o64 = psr.Options(precision=psr.PSR_FP64)
+        a64 = torch.empty((b.n, 3), dtype=torch.float64, device=dev)
+        lv.forces(o64, out=a64)
+        torch.cuda.synchronize()
+        e64 = []
+        for k in range(args.fp64_steps):
+            flush.fill_(k & 255)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            lv.forces(o64, out=a64)
+            s1.record(stream)
+            e64.append((s0, s1))
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(e) for a, e in e64) / args.fp64_steps
+        ref64 = a64.cpu().numpy()
+        d = acc32 - ref64
+        fp64 = {"value": evaluated / (ms64 / 1e3) / 1e9, "unit": "G pair-interactions/s",
+                "ms_per_step": ms64,
+                "fp32_table_rel_rms_vs_fp64_path": float(np.sqrt(np.sum(d * d) / np.sum(ref64 ** 2)))}
+
+    # end to end through the public API, host buffers, copies inside the region
+    e2e = None
+    if args.e2e_steps > 0:
+        pos_h = torch.from_numpy(b.pos).pin_memory()
+        out_h = torch.empty((b.n, 3), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            lv2 = psr.Leaves.build(pos_h.numpy(), b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
+            lv2.upload(dev)
+            out_h.copy_(lv2.forces(opts))
+            torch.cuda.synchronize()
+            h2d = int(lv2.info.device_bytes)
+            del lv2
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": world * evaluated / dt / 1e9, "unit": "G pair-interactions/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": b.n * 3 * 4,
+               "ms_per_step": dt * 1e3,
+               "includes": "host leaf/pair build, workspace upload, forward kernel, "
+                           "acceleration download"}
+
+    cb = err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, err, _ = cpu_baseline(b, acc32, args.cpu_targets)
+    pk, pk_src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOPS_PER_INTERACTION * evaluated / (mean_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": "G pair-interactions/s & % FP32 peak, FP32-table vs FP64 path, at stated force err",
+        "value": value, "unit": "G pair-interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": mean_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(b, args),
+        "interactions": {"evaluated_per_step": evaluated, "within_cutoff_per_step": within,
+                         "within_cutoff_value": world * within * args.steps / (total_ms / 1e3) / 1e9,
+                         "leaves": int(info.n_leaves), "leaf_pairs": int(info.n_pairs),
+                         "host_build_s": build_s},
+        "pct_fp32_peak_51flop": 100.0 * achieved / peak_tflops,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
+                                  % (props.multi_processor_count, sm_max, pk_src)},
+        "fp64_path": fp64,
+        "force_error": {"rel_rms_vs_fp64_oracle": err,
+                        "sampled_targets": None if cb is None else args.cpu_targets},
+        "e2e": e2e,
+        "cpu_baseline": None if cb is None else {k: cb[k] for k in
+                                                  ("value", "unit", "cores", "kind", "sample")},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "device": props.name,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_psr(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * psr.h - C ABI of libpsr, the GB300 (sm_103a) library for the truncated
+ * short-range particle-particle (P2P) gravity of the PM-FMM method
+ * (Wang & Meng, "PhotoNs-GPU", arXiv:2107.14008).
+ *
+ * What is computed (paper, Section 2, Eq. tr): for every particle i of a
+ * periodic box of side L,
+ *
+ *   a_i = G sum_j sum_{n in Z^3} [j != i or n != 0] [0 < |d| < r_c]
+ *           m_j d T(|d| / (2 r_s)) / |d|^3,      d = x_j + n L - x_i,
+ *   T(x) = erfc(x) + (2x / sqrt(pi)) exp(-x^2),
+ *
+ * i.e. the short-range pair force F_s = -(r/r^3) T of Section 2 per unit
+ * target mass, truncated at the cutoff r_c, with the split radius
+ * r_s = 1.2 L / N_PM.  The sum runs over the leaf pairs of an octree whose
+ * leaves hold at most max_leaf particles (Sections 2 and 3.1-3.2: particles
+ * grouped into contiguous leaves, a task list of <target leaf, source leaf>
+ * pairs grouped by target leaf).  The list holds every leaf pair whose
+ * bounding boxes come closer than r_c, so it adds no approximation.
+ *
+ * Conventions for every entry point:
+ *  - Status: 0 (PSR_OK) or a negative PSR_E_* code; psr_last_error() gives a
+ *    message (thread-local, valid until the next call on that thread).
+ *    Nothing throws across the ABI.
+ *  - Host pointers are marked "host", device pointers "device".  Device
+ *    memory is always owned by the caller; the library never allocates or
+ *    frees device memory and never synchronises inside psr_p2p_forces or
+ *    psr_p2p_adjoint (both only enqueue work on the given stream).
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Arrays of vectors are row-major n x 3.
+ *  - Calls that use the same psr_leaves must be ordered on one stream; two
+ *    such calls running concurrently on different streams race on the
+ *    workspace's scheduler counters.
+ */
+#ifndef PSR_H
+#define PSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define PSR_OK 0
+#define PSR_E_ARG (-1)       /* bad argument (NULL, size, NaN position ...)   */
+#define PSR_E_CUTOFF (-2)    /* r_c >= L or r_c <= 0: only n in {-1,0,1}^3
+                                images are summed, which needs r_c < L       */
+#define PSR_E_WORKSPACE (-3) /* workspace missing, too small or misaligned   */
+#define PSR_E_CUDA (-4)      /* a CUDA runtime call failed                   */
+#define PSR_E_DEVICE (-5)    /* a kernel's bounds check set the error word   */
+#define PSR_E_TIMEOUT (-6)   /* a bounded host wait on the device ran out    */
+#define PSR_E_NOMEM (-7)     /* host allocation failed                       */
+#define PSR_E_STATE (-8)     /* call order violated (e.g. not uploaded)      */
+
+/* ------------------------------------------------------------ options */
+/* precision of the pair arithmetic */
+#define PSR_FP64 0        /* FP64 throughout, T from erfc/exp               */
+#define PSR_FP32_EXACT 1  /* FP32 pair math, T from erfcf/expf              */
+#define PSR_FP32_TABLE 2  /* FP32 pair math, T interpolated from a table
+                             in shared memory (Section 3.3)                 */
+/* interpolation of the table (PSR_FP32_TABLE) */
+#define PSR_LINEAR 0      /* chord between nodes                            */
+#define PSR_CUBIC 1       /* cubic Hermite on (T_k, T'_k = x_k^2 E_k)       */
+/* accumulation of FP32 partial sums across source leaves */
+#define PSR_ACC_FP64 0    /* fold into FP64 accumulators                    */
+#define PSR_ACC_KAHAN32 1 /* fold with compensated (two-sum) FP32           */
+
+typedef struct {
+    double L;   /* box side; positions are wrapped into [0, L)              */
+    double r_s; /* split radius (1.2 L / N_PM in the paper, Section 2)      */
+    double r_c; /* cutoff radius, 0 < r_c < L                                */
+    double G;   /* gravitational constant                                    */
+} psr_box;
+
+typedef struct {
+    int precision;       /* PSR_FP64 | PSR_FP32_EXACT | PSR_FP32_TABLE        */
+    int table_n;         /* table intervals on [0, x_c], power of two in
+                            [64, 8192]; 0 = 1024                              */
+    int interp;          /* PSR_LINEAR | PSR_CUBIC                            */
+    int accum;           /* PSR_ACC_FP64 | PSR_ACC_KAHAN32                    */
+    int warps_per_block; /* 0 = default (8)                                   */
+    int blocks_per_sm;   /* 0 = default (occupancy-derived)                   */
+    int fold_every;      /* source particles summed in FP32 before a fold;
+                            0 = default (64)                                  */
+    int count_pairs;     /* 1: also count pairs with 0 < r < r_c (slower)     */
+    int reserved[8];     /* must be zero                                      */
+} psr_opts;
+
+typedef struct {
+    int64_t n;               /* particles (all boxes)                          */
+    int64_t n_leaves;        /* octree leaves                                  */
+    int64_t n_pairs;         /* leaf-pair entries (including i = j)            */
+    int64_t n_items;         /* scheduled target leaves (= n_leaves)           */
+    int64_t nbox;            /* boxes                                          */
+    int64_t evaluated_pairs; /* sum over leaf pairs of n_I * n_J               */
+    size_t device_bytes;     /* workspace size psr_upload needs                */
+    int max_leaf;            /* largest leaf occupancy                          */
+    int max_row;             /* most source leaves of one target leaf          */
+    double build_seconds;    /* host time of psr_build_leaves*                 */
+    const int64_t* perm;     /* host, n: sorted index -> original index
+                                (owned by the handle)                          */
+} psr_info;
+
+typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
+
+/* Build flags */
+#define PSR_BUILD_NO_FP64 1 /* omit the FP64 particle copy (PSR_FP64 and the
+                               FP64 adjoint are then unavailable)            */
+
+/*
+ * psr_build_leaves - host: sort particles along a Morton curve, cut the
+ * octree into leaves of at most max_leaf particles (each leaf a contiguous
+ * pack, Section 2), and build the near-field leaf-pair list grouped by
+ * target leaf (the TaskGroup/GroupIdx of Section 3.2) with a periodic image
+ * code per entry.
+ *   pos      host, n x 3 FP64, any real values (wrapped into [0, L))
+ *   mass     host, n FP64, or NULL for equal masses 1/n
+ *   box      host, box parameters
+ *   max_leaf 1..64
+ *   flags    PSR_BUILD_* bits
+ *   out      receives the handle; free with psr_free_leaves
+ * Errors: PSR_E_ARG (NULL, n < 1, n >= 2^31, non-finite input, max_leaf out
+ * of range, r_s <= 0), PSR_E_CUTOFF (r_c <= 0 or r_c >= L), PSR_E_NOMEM.
+ */
+int psr_build_leaves(const double* pos, const double* mass, int64_t n, const psr_box* box,
+                     int max_leaf, int flags, psr_leaves** out);
+
+/*
+ * psr_build_leaves_batch - host: as psr_build_leaves for nbox independent
+ * boxes in one handle; one launch then serves every box.  Particles are
+ * numbered box after box (box 0's n[0] particles first).  All boxes must
+ * share the ratio r_c / r_s (one interpolation table).
+ */
+int psr_build_leaves_batch(int nbox, const double* const* pos, const double* const* mass,
+                           const int64_t* n, const psr_box* boxes, int max_leaf, int flags,
+                           psr_leaves** out);
+
+/* psr_leaves_info - host: sizes of a built handle (see psr_info). */
+int psr_leaves_info(const psr_leaves* h, psr_info* info);
+
+/*
+ * psr_upload - copy the handle's arrays into a caller-owned device
+ * workspace of at least info.device_bytes bytes, 256-byte aligned, on
+ * `cuda_stream` (the host side is pageable, so the call returns once the
+ * copies are staged).  The workspace must stay allocated, and unchanged by
+ * the caller, while the handle uses it.
+ * Errors: PSR_E_WORKSPACE (NULL, too small, misaligned), PSR_E_CUDA.
+ */
+int psr_upload(psr_leaves* h, void* d_workspace, size_t bytes, void* cuda_stream);
+
+/*
+ * psr_p2p_forces - device: accelerations of every particle (Section 2 pair
+ * force, Section 3.2 kernel), one persistent launch over all target leaves
+ * of all boxes.
+ *   d_acc  device, n x 3, in the ORIGINAL particle order; FP64 when
+ *          opts->precision == PSR_FP64, FP32 otherwise.  Overwritten.
+ * The first call with a new (precision, table_n, interp) also builds the
+ * interpolation table in the workspace (one small extra launch).
+ * Errors: PSR_E_ARG, PSR_E_STATE (not uploaded; FP64 payload omitted),
+ * PSR_E_CUDA (launch failure).
+ */
+int psr_p2p_forces(psr_leaves* h, const psr_opts* opts, void* d_acc, void* cuda_stream);
+
+/*
+ * psr_p2p_adjoint - device: gradients of L = sum_i c_i . a_i (not in the
+ * paper; derived from the pair force and the n = 2 truncated prefactor f_(2)
+ * of Section 2):
+ *   dL/dx_k = G sum_j K(d_kj) (m_k c_j - m_j c_k),
+ *   K(d)    = g I + (g'(r)/r) d d^T,  g = T/r^3,  g'(r)/r = -f_(2),
+ *   dL/dm_k = -G sum_j g(r_kj) d_kj . c_j,
+ * over the same pairs as the forward sum.
+ *   d_cot       device, n x 3 cotangent, original order
+ *   d_grad_pos  device, n x 3, original order, overwritten
+ *   d_grad_mass device, n, original order, overwritten (may be NULL)
+ * All three are FP64 when opts->precision == PSR_FP64, FP32 otherwise.
+ */
+int psr_p2p_adjoint(psr_leaves* h, const psr_opts* opts, const void* d_cot, void* d_grad_pos,
+                    void* d_grad_mass, void* cuda_stream);
+
+/*
+ * psr_pair_count - host: number of pairs with 0 < r < r_c counted by the
+ * last psr_p2p_forces call made with opts->count_pairs = 1 (waits up to
+ * timeout_ms for the stream).  Errors: PSR_E_STATE, PSR_E_TIMEOUT.
+ */
+int psr_pair_count(psr_leaves* h, void* cuda_stream, int timeout_ms, int64_t* count);
+
+/*
+ * psr_check - host: wait (at most timeout_ms) for `cuda_stream`, then read
+ * and clear the workspace's device error word.  Returns PSR_E_DEVICE if a
+ * kernel found an out-of-range index (the offending entry was skipped),
+ * PSR_E_TIMEOUT if the stream did not finish in time.
+ */
+int psr_check(psr_leaves* h, void* cuda_stream, int timeout_ms);
+
+/*
+ * psr_table - device: write the interpolation table the FP32 table path
+ * uses for (table_n, interp) over [0, x_c] into d_out (float4 entries,
+ * table_n + 1 of them; entry table_n is the zero sentinel beyond the
+ * cutoff).  Linear: (M_k, D_k, 0, 0) with T = M_k + f D_k, f in
+ * [-1/2, 1/2] about the interval midpoint; cubic: (c0, c1, c2, c3) with
+ * T = c0 + f (c1 + f (c2 + f c3)).  For tests and inspection.
+ */
+int psr_table(int table_n, int interp, double x_c, void* d_out, void* cuda_stream);
+
+/*
+ * psr_leaves_host_arrays - host: read-only views of the handle's host copies
+ * of what psr_upload sends to the device (for tests and inspection).  Valid
+ * until psr_free_leaves.  Layouts:
+ *   pf     n x 4 FP32: (x, y, z) - leaf-cell centre, divided by 2 r_s; mass
+ *   pd     n x 4 FP64: wrapped x, y, z; mass (NULL with PSR_BUILD_NO_FP64)
+ *   leaf   n_leaves x 4 int32: first sorted particle, count, box, 0
+ *   lcen   n_leaves x 4 int32: cell centre in units of L / 2^22 (x, y, z),
+ *          octree level
+ *   rowptr n_leaves + 1 int64: entries of target leaf I are
+ *          pairs[rowptr[I] .. rowptr[I+1])
+ *   pairs  n_pairs uint32: (source leaf << 5) | (nx+1)*9 + (ny+1)*3 + (nz+1)
+ *   items  n_leaves int32: target leaves in the order the kernels take them
+ */
+typedef struct {
+    const float* pf;
+    const double* pd;
+    const int32_t* leaf;
+    const int32_t* lcen;
+    const int64_t* rowptr;
+    const uint32_t* pairs;
+    const int32_t* items;
+} psr_host_arrays;
+int psr_leaves_host_arrays(const psr_leaves* h, psr_host_arrays* out);
+
+/* psr_free_leaves - host: free a handle (NULL is ignored). */
+void psr_free_leaves(psr_leaves* h);
+
+/* psr_last_error - message of the last failing call on this thread. */
+const char* psr_last_error(void);
+
+/* psr_version - library version string. */
+const char* psr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSR_H */

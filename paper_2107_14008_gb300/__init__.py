@@ -1,0 +1,251 @@
+"""psr: GB300-native truncated short-range P2P gravity (arXiv:2107.14008).
+
+Python layer over libpsr's C ABI: argument marshalling, device memory from
+PyTorch, and a torch.autograd.Function.  Every step of the computation runs
+in libpsr (host leaf builder in C++, forward/adjoint/table kernels in CUDA
+for sm_103a).  There is no CPU fallback: without the built library, or
+without a CUDA device, the device calls raise.
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import capi
+from .capi import (PSR_ACC_FP64, PSR_ACC_KAHAN32, PSR_CUBIC, PSR_FP32_EXACT, PSR_FP32_TABLE,
+                   PSR_FP64, PSR_LINEAR, PsrError)
+
+__all__ = ["Options", "Leaves", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
+           "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_ACC_FP64", "PSR_ACC_KAHAN32"]
+
+
+@dataclass
+class Options:
+    """Kernel options (psr_opts)."""
+    precision: int = PSR_FP32_TABLE
+    table_n: int = 1024
+    interp: int = PSR_LINEAR
+    accum: int = PSR_ACC_FP64
+    warps_per_block: int = 0
+    blocks_per_sm: int = 0
+    fold_every: int = 0
+    count_pairs: bool = False
+
+    def c(self):
+        o = capi.psr_opts()
+        o.precision, o.table_n, o.interp, o.accum = (int(self.precision), int(self.table_n),
+                                                     int(self.interp), int(self.accum))
+        o.warps_per_block, o.blocks_per_sm = int(self.warps_per_block), int(self.blocks_per_sm)
+        o.fold_every, o.count_pairs = int(self.fold_every), int(bool(self.count_pairs))
+        return o
+
+    @property
+    def fp64(self):
+        return self.precision == PSR_FP64
+
+
+def _box(L, r_s, r_c, G=1.0):
+    return capi.psr_box(float(L), float(r_s), float(r_c), float(G))
+
+
+def _host_f64(a, cols):
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(-1, cols) if cols > 1 else a.reshape(-1)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Leaves:
+    """A built leaf set (psr_leaves handle) and, once uploaded, its device
+    workspace (a torch uint8 tensor owned by this object)."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+        self.workspace = None
+        self._info = capi.psr_leaves_info(handle)
+
+    @classmethod
+    def build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True):
+        p = _host_f64(pos, 3)
+        m = None if mass is None else _host_f64(mass, 1)
+        if m is not None and m.shape[0] != p.shape[0]:
+            raise ValueError("mass and pos lengths differ")
+        dp = ctypes.POINTER(ctypes.c_double)
+        h = capi.psr_build_leaves(p.ctypes.data_as(dp),
+                                  None if m is None else m.ctypes.data_as(dp), p.shape[0],
+                                  _box(L, r_s, r_c, G), int(max_leaf),
+                                  0 if fp64 else capi.PSR_BUILD_NO_FP64)
+        return cls(h, p.shape[0])
+
+    @classmethod
+    def build_batch(cls, boxes, max_leaf=32, fp64=True):
+        """boxes: sequence of (pos, mass, L, r_s, r_c, G)."""
+        dp = ctypes.POINTER(ctypes.c_double)
+        keep, pp, mm, ns, bx = [], [], [], [], []
+        for (pos, mass, L, r_s, r_c, G) in boxes:
+            p = _host_f64(pos, 3)
+            m = _host_f64(mass, 1) if mass is not None else np.full(p.shape[0], 1.0 / p.shape[0])
+            keep += [p, m]
+            pp.append(p.ctypes.data_as(dp))
+            mm.append(m.ctypes.data_as(dp))
+            ns.append(p.shape[0])
+            bx.append(_box(L, r_s, r_c, G))
+        nb = len(boxes)
+        h = capi.psr_build_leaves_batch(nb, (dp * nb)(*pp), (dp * nb)(*mm),
+                                        (ctypes.c_int64 * nb)(*ns), (capi.psr_box * nb)(*bx),
+                                        int(max_leaf), 0 if fp64 else capi.PSR_BUILD_NO_FP64)
+        return cls(h, int(sum(ns)))
+
+    # -- host-side information -------------------------------------------
+    @property
+    def info(self):
+        return self._info
+
+    @property
+    def perm(self):
+        return np.ctypeslib.as_array(self._info.perm, shape=(self.n,)).copy()
+
+    def host_arrays(self):
+        """Copies of the host arrays psr_upload sends (see psr_leaves_host_arrays)."""
+        a = capi.psr_leaves_host_arrays(self._h)
+        inf = self._info
+        nl, npairs = int(inf.n_leaves), int(inf.n_pairs)
+        v = lambda p, shape: np.ctypeslib.as_array(p, shape=shape).copy()
+        out = {"pf": v(a.pf, (self.n, 4)), "leaf": v(a.leaf, (nl, 4)), "lcen": v(a.lcen, (nl, 4)),
+               "rowptr": v(a.rowptr, (nl + 1,)),
+               "pairs": v(a.pairs, (npairs,)) if npairs else np.zeros(0, np.uint32),
+               "items": v(a.items, (nl,))}
+        out["pd"] = v(a.pd, (self.n, 4)) if bool(a.pd) else None
+        return out
+
+    @property
+    def evaluated_pairs(self):
+        return int(self._info.evaluated_pairs)
+
+    # -- device ---------------------------------------------------------------
+    def upload(self, device=None, stream=None):
+        import torch
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        nbytes = int(self._info.device_bytes)
+        if self.workspace is None or self.workspace.numel() < nbytes or self.workspace.device != dev:
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
+            capi.psr_upload(self._h, self.workspace.data_ptr(), self.workspace.numel(),
+                            _stream_handle(stream))
+        return self
+
+    def _dev(self):
+        if self.workspace is None:
+            raise PsrError(capi.PSR_E_STATE, "upload() has not been called")
+        return self.workspace.device
+
+    def forces(self, opts=None, out=None, stream=None):
+        """Accelerations (n,3) on the workspace's device, original order."""
+        import torch
+        opts = opts or Options()
+        dt = torch.float64 if opts.fp64 else torch.float32
+        dev = self._dev()
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=dt, device=dev)
+        if out.dtype != dt or out.shape != (self.n, 3) or not out.is_contiguous() or out.device != dev:
+            raise ValueError("out must be a contiguous (n,3) %s tensor on %s" % (dt, dev))
+        with torch.cuda.device(dev):
+            capi.psr_p2p_forces(self._h, opts.c(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def adjoint(self, cot, opts=None, grad_pos=None, grad_mass=None, stream=None):
+        """(dL/dx (n,3), dL/dm (n,)) for L = sum_i cot_i . a_i."""
+        import torch
+        opts = opts or Options()
+        dt = torch.float64 if opts.fp64 else torch.float32
+        dev = self._dev()
+        cot = cot.to(device=dev, dtype=dt).contiguous()
+        if cot.shape != (self.n, 3):
+            raise ValueError("cotangent must be (n,3)")
+        if grad_pos is None:
+            grad_pos = torch.empty((self.n, 3), dtype=dt, device=dev)
+        if grad_mass is None:
+            grad_mass = torch.empty((self.n,), dtype=dt, device=dev)
+        with torch.cuda.device(dev):
+            capi.psr_p2p_adjoint(self._h, opts.c(), cot.data_ptr(), grad_pos.data_ptr(),
+                                 grad_mass.data_ptr(), _stream_handle(stream))
+        return grad_pos, grad_mass
+
+    def pair_count(self, stream=None, timeout_ms=60000):
+        return capi.psr_pair_count(self._h, _stream_handle(stream), timeout_ms)
+
+    def check(self, stream=None, timeout_ms=60000):
+        return capi.psr_check(self._h, _stream_handle(stream), timeout_ms)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            capi.psr_free_leaves(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class P2PForce(torch.autograd.Function):
+        """a = P2PForce.apply(pos, mass, L, r_s, r_c, G, opts, max_leaf).
+
+        Forward builds the leaf set on the host from `pos` and runs the
+        forward kernel; backward runs the adjoint kernel on the same pair set
+        (the set is frozen at the forward positions, so the gradient is that
+        of the piecewise function with the hard cutoff held fixed)."""
+
+        @staticmethod
+        def forward(ctx, pos, mass, L, r_s, r_c, G=1.0, opts=None, max_leaf=32):
+            opts = opts or Options()
+            lv = Leaves.build(pos, mass, L, r_s, r_c, G, max_leaf, fp64=opts.fp64)
+            lv.upload(pos.device)
+            acc = lv.forces(opts)
+            ctx.leaves, ctx.opts = lv, opts
+            ctx.pos_dtype, ctx.mass_dtype = pos.dtype, mass.dtype
+            return acc.to(pos.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_acc):
+            gp, gm = ctx.leaves.adjoint(grad_acc.contiguous(), ctx.opts)
+            return (gp.to(ctx.pos_dtype), gm.to(ctx.mass_dtype), None, None, None, None, None,
+                    None)
+
+    return P2PForce
+
+
+class _Lazy:
+    _f = None
+
+    def __get__(self, obj, owner):
+        if _Lazy._f is None:
+            _Lazy._f = _autograd_function()
+        return _Lazy._f
+
+
+class _Namespace:
+    P2PForce = _Lazy()
+
+
+def __getattr__(name):
+    if name == "P2PForce":
+        return _Namespace.P2PForce
+    raise AttributeError(name)
+
+
+def forces(pos, mass, L, r_s, r_c, G=1.0, opts=None, max_leaf=32):
+    """Differentiable accelerations of particles `pos` (torch, CUDA)."""
+    return _Namespace.P2PForce.apply(pos, mass, L, r_s, r_c, G, opts, max_leaf)

@@ -1,0 +1,354 @@
+// C ABI of libpsr (declared in include/psr.h): argument checks, workspace
+// upload, table caching and kernel launches.  No device allocation happens
+// here; psr_p2p_forces and psr_p2p_adjoint only enqueue work.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+
+#include "psr_internal.h"
+
+using namespace psr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(PSR_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Poll the stream until it is idle or timeout_ms has passed.
+int wait_stream(cudaStream_t st, int timeout_ms)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return PSR_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > timeout_ms) return fail(PSR_E_TIMEOUT, "stream did not finish within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+struct Opts {
+    int precision, table_n, interp, accum, warps, bps, fold, count;
+};
+
+int check_opts(const psr_opts* o, Opts* out)
+{
+    psr_opts d{};
+    d.precision = PSR_FP32_TABLE;
+    if (!o) o = &d;
+    for (int i = 0; i < 8; ++i)
+        if (o->reserved[i] != 0) return fail(PSR_E_ARG, "psr_opts.reserved must be zero");
+    if (o->precision < PSR_FP64 || o->precision > PSR_FP32_TABLE)
+        return fail(PSR_E_ARG, "psr_opts.precision out of range");
+    int tn = o->table_n ? o->table_n : 1024;
+    if (tn < 64 || tn > kMaxTableN || (tn & (tn - 1)))
+        return fail(PSR_E_ARG, "psr_opts.table_n must be a power of two in [64, 8192]");
+    if (o->interp != PSR_LINEAR && o->interp != PSR_CUBIC)
+        return fail(PSR_E_ARG, "psr_opts.interp out of range");
+    if (o->accum != PSR_ACC_FP64 && o->accum != PSR_ACC_KAHAN32)
+        return fail(PSR_E_ARG, "psr_opts.accum out of range");
+    int w = o->warps_per_block ? o->warps_per_block : 8;
+    if (w < 1 || w > 8) return fail(PSR_E_ARG, "psr_opts.warps_per_block must be in [1, 8]");
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64)
+        return fail(PSR_E_ARG, "psr_opts.blocks_per_sm must be in [0, 64]");
+    int fold = o->fold_every ? o->fold_every : 64;
+    if (fold < 1) return fail(PSR_E_ARG, "psr_opts.fold_every must be positive");
+    *out = Opts{o->precision, tn, o->interp, o->accum, w, o->blocks_per_sm, fold, o->count_pairs ? 1 : 0};
+    return PSR_OK;
+}
+
+FwdArgs base_args(Leaves* h, const Opts& o)
+{
+    FwdArgs a{};
+    char* w = h->d_ws;
+    const Layout& L = h->lay;
+    a.pf = w + L.pf;
+    a.pd = h->pd.empty() ? nullptr : w + L.pd;
+    a.perm = reinterpret_cast<const int32_t*>(w + L.perm);
+    a.leaf = reinterpret_cast<const int32_t*>(w + L.leaf);
+    a.lcen = reinterpret_cast<const int32_t*>(w + L.lcen);
+    a.rowptr = reinterpret_cast<const int64_t*>(w + L.rowptr);
+    a.pairs = reinterpret_cast<const uint32_t*>(w + L.pairs);
+    a.items = reinterpret_cast<const int32_t*>(w + L.items);
+    a.boxes = reinterpret_cast<const BoxDev*>(w + L.boxes);
+    a.table = w + L.table;
+    a.ctrl = reinterpret_cast<unsigned*>(w + L.ctrl);
+    a.cot_sorted = w + L.cotf;
+    a.n = h->n;
+    a.n_leaves = (int64_t)(h->leaf.size() / 4);
+    a.n_pairs = (int64_t)h->pairs.size();
+    a.n_items = (int)h->items.size();
+    a.nbox = h->nbox;
+    a.table_n = o.table_n;
+    a.interp = o.interp;
+    a.accum = o.accum;
+    a.fold_every = o.fold;
+    a.count_pairs = o.count;
+    a.warps_per_block = o.warps;
+    a.max_leaf = h->max_leaf;
+    return a;
+}
+
+int ensure_table(Leaves* h, const Opts& o, cudaStream_t st)
+{
+    if (o.precision != PSR_FP32_TABLE) return PSR_OK;
+    const double x_c = h->boxes[0].r_c / (2.0 * h->boxes[0].r_s);
+    int key = o.table_n * 2 + o.interp;
+    if (key == h->table_key && x_c == h->table_xc) return PSR_OK;
+    char* t = h->d_ws + h->lay.table;
+    int e = launch_table(o.table_n, o.interp, x_c, t, t + (size_t)(kMaxTableN + 1) * 16, st);
+    if (e) return cuda_fail((cudaError_t)e, "table kernel launch");
+    h->table_key = key;
+    h->table_xc = x_c;
+    return PSR_OK;
+}
+
+int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
+{
+    int bps = o.bps;
+    if (bps == 0) {
+        int occ = 0, e;
+        if (adjoint)
+            e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n, &occ);
+        else if (o.precision == PSR_FP64)
+            e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
+        else
+            e = fwd_f32_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n, &occ);
+        if (e) return cuda_fail((cudaError_t)e, "occupancy query");
+        bps = occ > 0 ? occ : 1;
+    }
+    *blocks = bps * (h->sm_count > 0 ? h->sm_count : 1);
+    return PSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* psr_last_error(void) { return g_err.c_str(); }
+
+const char* psr_version(void) { return "psr 0.1 (sm_103a)"; }
+
+int psr_build_leaves(const double* pos, const double* mass, int64_t n, const psr_box* box,
+                     int max_leaf, int flags, psr_leaves** out)
+{
+    if (!box) return fail(PSR_E_ARG, "null box");
+    const double* p[1] = {pos};
+    const double* m[1] = {mass};
+    int64_t nn[1] = {n};
+    Leaves* h = nullptr;
+    std::string err;
+    int rc = build_batch(1, p, mass ? m : nullptr, nn, box, max_leaf, flags, &h, &err);
+    if (rc) return fail(rc, err);
+    *out = reinterpret_cast<psr_leaves*>(h);
+    return PSR_OK;
+}
+
+int psr_build_leaves_batch(int nbox, const double* const* pos, const double* const* mass,
+                           const int64_t* n, const psr_box* boxes, int max_leaf, int flags,
+                           psr_leaves** out)
+{
+    Leaves* h = nullptr;
+    std::string err;
+    int rc = build_batch(nbox, pos, mass, n, boxes, max_leaf, flags, &h, &err);
+    if (rc) return fail(rc, err);
+    *out = reinterpret_cast<psr_leaves*>(h);
+    return PSR_OK;
+}
+
+int psr_leaves_info(const psr_leaves* hh, psr_info* info)
+{
+    const Leaves* h = reinterpret_cast<const Leaves*>(hh);
+    if (!h || !info) return fail(PSR_E_ARG, "null argument");
+    std::memset(info, 0, sizeof *info);
+    info->n = h->n;
+    info->n_leaves = (int64_t)(h->leaf.size() / 4);
+    info->n_pairs = (int64_t)h->pairs.size();
+    info->n_items = (int64_t)h->items.size();
+    info->nbox = h->nbox;
+    info->evaluated_pairs = h->evaluated;
+    info->device_bytes = h->lay.total;
+    info->max_leaf = h->max_leaf;
+    info->max_row = h->max_row;
+    info->build_seconds = h->build_seconds;
+    info->perm = h->perm.data();
+    return PSR_OK;
+}
+
+int psr_upload(psr_leaves* hh, void* d_ws, size_t bytes, void* stream)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h) return fail(PSR_E_ARG, "null handle");
+    if (!d_ws || bytes < h->lay.total || (reinterpret_cast<uintptr_t>(d_ws) & 255))
+        return fail(PSR_E_WORKSPACE, "workspace must be 256-byte aligned and at least " +
+                                         std::to_string(h->lay.total) + " bytes");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    char* w = static_cast<char*>(d_ws);
+    const Layout& L = h->lay;
+    struct Cp { size_t off; const void* src; size_t bytes; } cps[] = {
+        {L.pf, h->pf.data(), h->pf.size() * sizeof(float)},
+        {L.pd, h->pd.data(), h->pd.size() * sizeof(double)},
+        {L.perm, h->perm32.data(), h->perm32.size() * sizeof(int32_t)},
+        {L.leaf, h->leaf.data(), h->leaf.size() * sizeof(int32_t)},
+        {L.lcen, h->lcen.data(), h->lcen.size() * sizeof(int32_t)},
+        {L.rowptr, h->rowptr.data(), h->rowptr.size() * sizeof(int64_t)},
+        {L.pairs, h->pairs.data(), h->pairs.size() * sizeof(uint32_t)},
+        {L.items, h->items.data(), h->items.size() * sizeof(int32_t)},
+        {L.boxes, h->boxdev.data(), h->boxdev.size() * sizeof(BoxDev)},
+    };
+    for (const Cp& c : cps) {
+        if (!c.bytes) continue;
+        if ((e = cudaMemcpyAsync(w + c.off, c.src, c.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync (upload)");
+    }
+    if ((e = cudaMemsetAsync(w + L.ctrl, 0, kCtrlWords * 4, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync (ctrl)");
+    h->d_ws = w;
+    h->ws_bytes = bytes;
+    h->uploaded = true;
+    h->table_key = -1;
+    h->table_xc = -1.0;
+    h->sm_count = sms;
+    h->device = dev;
+    return PSR_OK;
+}
+
+int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stream)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h || !d_acc) return fail(PSR_E_ARG, "null argument");
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    Opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (o.precision == PSR_FP64 && h->pd.empty())
+        return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_table(h, o, st))) return rc;
+    FwdArgs a = base_args(h, o);
+    a.out = d_acc;
+    if ((rc = grid_blocks(h, o, 0, &a.blocks))) return rc;
+    if (o.count) {
+        cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 8, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (pair counter)");
+    }
+    int e = (o.precision == PSR_FP64) ? launch_fwd_f64(a, st) : launch_fwd_f32(a, o.precision, st);
+    if (e) return cuda_fail((cudaError_t)e, "forward kernel launch");
+    return PSR_OK;
+}
+
+int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, void* d_grad_pos,
+                    void* d_grad_mass, void* stream)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h || !d_cot || !d_grad_pos) return fail(PSR_E_ARG, "null argument");
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    Opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (o.precision == PSR_FP64 && h->pd.empty())
+        return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
+    if (o.precision == PSR_FP32_TABLE && o.interp == PSR_CUBIC && o.table_n > 4096)
+        return fail(PSR_E_ARG, "cubic adjoint tables hold at most 4096 intervals (shared memory)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_table(h, o, st))) return rc;
+    FwdArgs a = base_args(h, o);
+    a.cot = d_cot;
+    a.out = d_grad_pos;
+    a.out_m = d_grad_mass;
+    if ((rc = grid_blocks(h, o, 1, &a.blocks))) return rc;
+    int e = (o.precision == PSR_FP64) ? launch_adj_f64(a, st) : launch_adj_f32(a, o.precision, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint kernel launch");
+    return PSR_OK;
+}
+
+int psr_pair_count(psr_leaves* hh, void* stream, int timeout_ms, int64_t* count)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h || !count) return fail(PSR_E_ARG, "null argument");
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = wait_stream(st, timeout_ms);
+    if (rc) return rc;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->d_ws + h->lay.ctrl + kCtrlPairsLo * 4, 8,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (pair counter)");
+    if ((rc = wait_stream(st, timeout_ms))) return rc;
+    *count = (int64_t)v;
+    return PSR_OK;
+}
+
+int psr_check(psr_leaves* hh, void* stream, int timeout_ms)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h) return fail(PSR_E_ARG, "null handle");
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = wait_stream(st, timeout_ms);
+    if (rc) return rc;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    unsigned v = 0;
+    e = cudaMemcpyAsync(&v, h->d_ws + h->lay.ctrl + kCtrlError * 4, 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (error word)");
+    if ((rc = wait_stream(st, timeout_ms))) return rc;
+    if (v) {
+        e = cudaMemsetAsync(h->d_ws + h->lay.ctrl + kCtrlError * 4, 0, 4, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (error word)");
+        if ((rc = wait_stream(st, timeout_ms))) return rc;
+        return fail(PSR_E_DEVICE, "device bounds check failed, error bits 0x" + std::to_string(v));
+    }
+    return PSR_OK;
+}
+
+int psr_table(int table_n, int interp, double x_c, void* d_out, void* stream)
+{
+    if (!d_out) return fail(PSR_E_ARG, "null output");
+    if (table_n < 64 || table_n > kMaxTableN || (table_n & (table_n - 1)))
+        return fail(PSR_E_ARG, "table_n must be a power of two in [64, 8192]");
+    if (interp != PSR_LINEAR && interp != PSR_CUBIC) return fail(PSR_E_ARG, "interp out of range");
+    if (!(x_c > 0) || !std::isfinite(x_c)) return fail(PSR_E_ARG, "x_c must be positive");
+    int e = launch_table(table_n, interp, x_c, d_out, nullptr, stream);
+    if (e) return cuda_fail((cudaError_t)e, "table kernel launch");
+    return PSR_OK;
+}
+
+int psr_leaves_host_arrays(const psr_leaves* hh, psr_host_arrays* out)
+{
+    const Leaves* h = reinterpret_cast<const Leaves*>(hh);
+    if (!h || !out) return fail(PSR_E_ARG, "null argument");
+    out->pf = h->pf.data();
+    out->pd = h->pd.empty() ? nullptr : h->pd.data();
+    out->leaf = h->leaf.data();
+    out->lcen = h->lcen.data();
+    out->rowptr = h->rowptr.data();
+    out->pairs = h->pairs.data();
+    out->items = h->items.data();
+    return PSR_OK;
+}
+
+void psr_free_leaves(psr_leaves* hh) { delete reinterpret_cast<Leaves*>(hh); }
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations shared by the host builder, the C ABI and the CUDA
+// kernels of libpsr.  Not part of the public ABI (see include/psr.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/psr.h"
+
+namespace psr {
+
+// Positions are quantised to 21 bits per axis for the Morton order; leaf-cell
+// centres are integers in units of L / 2^22 (a cell of level l and index i has
+// its centre at (2i + 1) 2^(21 - l)), so centre differences, with a periodic
+// shift of n * 2^22, are integers below 2^24 in magnitude and convert to FP32
+// exactly.
+constexpr int kMortonBits = 21;
+constexpr int kCentreShift = 22;
+constexpr int kMaxLeaf = 64;
+constexpr int kShiftCodes = 27;  // (nx+1)*9 + (ny+1)*3 + (nz+1)
+constexpr int kMaxTableN = 8192;
+
+// Per-box constants as the kernels see them (plain old data, 16B aligned).
+struct alignas(16) BoxDev {
+    double L, r_s, r_c, G;      // FP64 path
+    double rc2, inv_2rs, pad0, pad1;
+    float unit;     // (L / 2^22) / (2 r_s): centre units -> FP32 coordinate units
+    float x_c;      // r_c / (2 r_s): cutoff in FP32 coordinate units (= x)
+    float x_c2;     // x_c^2
+    float g_acc;    // G / (2 r_s)^2: FP32 coordinate sums -> acceleration
+    float g_adj;    // G / (8 r_s^3): adjoint position gradient factor
+    float g_adjm;   // G / (4 r_s^2): adjoint mass gradient factor
+    float pad2, pad3;
+};
+static_assert(sizeof(BoxDev) == 96, "BoxDev layout");
+
+// Byte offsets of the regions of the device workspace (256-byte aligned).
+struct Layout {
+    size_t pf;       // float4[n]    FP32 leaf-local coords / (2 r_s), mass
+    size_t pd;       // double4[n]   FP64 wrapped coords, mass (optional)
+    size_t perm;     // int32[n]     sorted -> original
+    size_t leaf;     // int4[nl]     first, count, box, pad
+    size_t lcen;     // int4[nl]     centre x, y, z (units L/2^22), level
+    size_t rowptr;   // int64[nl+1]  CSR of pair entries by target leaf
+    size_t pairs;    // uint32[np]   (source leaf << 5) | shift code
+    size_t items;    // int32[nl]    target leaves in schedule order
+    size_t boxes;    // BoxDev[nbox]
+    size_t table;    // float4[2 * (kMaxTableN + 1)]: T table, then exp(-x^2)
+    size_t cotf;     // float4[n] / double4[n] adjoint source payload scratch
+    size_t ctrl;     // uint32[64]  scheduler tickets, error word, counters
+    size_t total;
+};
+
+// ctrl word indices
+enum : int {
+    kCtrlTicketFwd = 0,
+    kCtrlDoneFwd = 1,
+    kCtrlTicketAdj = 2,
+    kCtrlDoneAdj = 3,
+    kCtrlError = 8,
+    kCtrlPairsLo = 16,  // uint64 at words 16..17
+    kCtrlWords = 64,
+};
+// error bits
+enum : unsigned {
+    kErrLeafIndex = 1u,
+    kErrParticleRange = 2u,
+    kErrItemIndex = 4u,
+    kErrShiftCode = 8u,
+};
+
+struct Leaves {
+    int nbox = 0;
+    std::vector<psr_box> boxes;
+    std::vector<BoxDev> boxdev;
+    std::vector<int64_t> box_first;  // first particle of each box (original numbering)
+    int64_t n = 0;
+    int max_leaf_req = 0;
+    int flags = 0;
+    double build_seconds = 0.0;
+    // sorted particles
+    std::vector<float> pf;     // 4 per particle
+    std::vector<double> pd;    // 4 per particle
+    std::vector<int32_t> perm32;
+    std::vector<int64_t> perm;
+    // leaves
+    std::vector<int32_t> leaf;  // 4 per leaf
+    std::vector<int32_t> lcen;  // 4 per leaf
+    std::vector<int64_t> rowptr;
+    std::vector<uint32_t> pairs;
+    std::vector<int32_t> items;
+    int64_t evaluated = 0;
+    int max_leaf = 0;
+    int max_row = 0;
+    // device state
+    Layout lay{};
+    char* d_ws = nullptr;
+    size_t ws_bytes = 0;
+    bool uploaded = false;
+    int table_key = -1;       // cached forward table (n, interp) encoding
+    double table_xc = -1.0;
+    int adj_table_key = -1;
+    int sm_count = 0;
+    int device = -1;
+};
+
+// builder.cpp
+int build_batch(int nbox, const double* const* pos, const double* const* mass, const int64_t* n,
+                const psr_box* boxes, int max_leaf, int flags, Leaves** out, std::string* err);
+Layout make_layout(const Leaves& h);
+
+// kernels (launchers defined in the .cu files; return cudaError_t as int)
+struct FwdArgs {
+    const void* pf;
+    const void* pd;
+    const int32_t* perm;
+    const int32_t* leaf;
+    const int32_t* lcen;
+    const int64_t* rowptr;
+    const uint32_t* pairs;
+    const int32_t* items;
+    const BoxDev* boxes;
+    const void* table;   // float4[(table_n + 1)] forward, then Q table
+    unsigned* ctrl;
+    const void* cot;     // adjoint: cotangent, original order
+    void* cot_sorted;    // adjoint: sorted payload scratch
+    void* out;           // forward: acc; adjoint: grad pos
+    void* out_m;         // adjoint: grad mass (may be null)
+    int64_t n;
+    int64_t n_leaves;
+    int64_t n_pairs;
+    int n_items;
+    int nbox;
+    int table_n;
+    int interp;
+    int accum;
+    int fold_every;
+    int count_pairs;
+    int warps_per_block;
+    int blocks;
+    int max_leaf;
+};
+
+int launch_table(int table_n, int interp, double x_c, void* d_out, void* d_q_out, void* stream);
+int launch_fwd_f32(const FwdArgs& a, int precision, void* stream);
+int launch_fwd_f64(const FwdArgs& a, void* stream);
+int launch_adj_f32(const FwdArgs& a, int precision, void* stream);
+int launch_adj_f64(const FwdArgs& a, void* stream);
+int fwd_f32_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
+                      int* out);
+int fwd_f64_occupancy(int warps, int max_leaf, int* out);
+int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
+                  int* out);
+
+}  // namespace psr

@@ -1,0 +1,235 @@
+"""Host-side tests of libpsr: exported symbols, leaf partition, pair-list
+completeness against the oracle's within-cutoff pair counts, and argument
+errors.  No GPU is touched (psr_build_leaves is host code)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+psr = pytest.importorskip("paper_2107_14008_gb300")
+from paper_2107_14008_gb300 import capi  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2107_14008_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_declared_symbol():
+    text = open(os.path.join(ROOT, "include", "psr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    declared = sorted(set(re.findall(r"\b(psr_[a-z0-9_]+)\s*\(", text)))
+    assert declared, "no declarations found"
+    assert sorted(capi.EXPORTS) == declared
+    lib = ctypes.CDLL(capi.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert capi.psr_version().startswith("psr")
+
+
+def _build(b, max_leaf=32, fp64=True):
+    return psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf, fp64=fp64)
+
+
+def _clustered(n=4000, L=60.0, seed=3, n_pm=16):
+    rng = np.random.default_rng(seed)
+    pos, _ = synth.nfw_clustered(n, L, 0.6, 6, rng)
+    r_s, r_c = synth.box_params(L, n_pm)
+    return synth.Box(pos=pos, mass=rng.uniform(0.2, 2.0, n), L=L, n_pm=n_pm, r_s=r_s, r_c=r_c)
+
+
+def _small_box():
+    # r_c = 0.675 L: two images of one source can lie within r_c
+    rng = np.random.default_rng(4)
+    L, n = 10.0, 300
+    r_s, r_c = synth.box_params(L, 8)
+    return synth.Box(pos=rng.random((n, 3)) * L, mass=np.full(n, 1.0 / n), L=L, n_pm=8,
+                     r_s=r_s, r_c=r_c)
+
+
+CASES = {
+    "uniform": lambda: synth.small(nside=16),
+    "clustered": _clustered,
+    "small_box": _small_box,
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("max_leaf", [1, 8, 32, 64])
+def test_leaf_partition_and_local_coordinates(case, max_leaf):
+    b = CASES[case]()
+    lv = _build(b, max_leaf)
+    A = lv.host_arrays()
+    perm = lv.perm
+    n = b.n
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    leaf = A["leaf"]
+    assert leaf[0, 0] == 0
+    assert np.all(leaf[1:, 0] == leaf[:-1, 0] + leaf[:-1, 1])  # contiguous packs
+    assert leaf[-1, 0] + leaf[-1, 1] == n
+    assert leaf[:, 1].min() >= 1 and leaf[:, 1].max() <= max_leaf
+    assert lv.info.max_leaf == leaf[:, 1].max()
+    # FP64 copy is the wrapped position in sorted order
+    wrapped = np.mod(b.pos, b.L)
+    np.testing.assert_array_equal(A["pd"][:, :3], wrapped[perm])
+    np.testing.assert_array_equal(A["pd"][:, 3], b.mass[perm])
+    # FP32 local coordinates: (x - cell centre) / (2 r_s), inside the cell
+    unit = b.L / 2.0 ** 22
+    owner = np.repeat(np.arange(leaf.shape[0]), leaf[:, 1])
+    cen = A["lcen"][owner, :3] * unit
+    half = 0.5 * b.L / 2.0 ** A["lcen"][owner, 3]
+    loc = A["pf"][:, :3].astype(np.float64) * 2 * b.r_s
+    assert np.all(np.abs(loc) <= half[:, None] * (1 + 1e-6) + 1e-12)
+    # one FP32 rounding of a coordinate bounded by the cell's half side
+    err = np.abs(loc + cen - wrapped[perm])
+    assert np.all(err <= 1.2e-7 * half[:, None] + 1e-12 * b.L)
+    # centres are odd multiples of 2^(21 - level)
+    lc = A["lcen"]
+    step = 2 ** (21 - lc[:, 3])
+    assert np.all((lc[:, :3] // step[:, None]) % 2 == 1)
+
+
+def _count_listed_pairs(lv, b):
+    """Within-cutoff pairs per sorted target, summed over the leaf-pair list."""
+    A = lv.host_arrays()
+    pd, leaf, rowptr, pairs = A["pd"], A["leaf"], A["rowptr"], A["pairs"]
+    counts = np.zeros(b.n, dtype=np.int64)
+    for I in range(leaf.shape[0]):
+        f, c = leaf[I, 0], leaf[I, 1]
+        xi = pd[f:f + c, :3]
+        ent = pairs[rowptr[I]:rowptr[I + 1]]
+        seen = set()
+        for e in ent:
+            J, code = int(e >> 5), int(e & 31)
+            assert code < 27 and J < leaf.shape[0]
+            assert (J, code) not in seen
+            seen.add((J, code))
+            nvec = np.array([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1]) * b.L
+            xj = pd[leaf[J, 0]:leaf[J, 0] + leaf[J, 1], :3] + nvec
+            d = xj[None, :, :] - xi[:, None, :]
+            r2 = np.einsum("ijk,ijk->ij", d, d)
+            counts[f:f + c] += np.sum((r2 < b.r_c ** 2) & (r2 > 0), axis=1)
+        # the self pair (I, I, no shift) is always listed
+        assert (I, 13) in seen
+    return counts
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_pair_list_is_complete(case):
+    """Every pair within r_c appears in exactly one listed leaf pair: the
+    per-target counts equal the oracle's brute-force counts."""
+    b = CASES[case]()
+    lv = _build(b, 16)
+    counts = _count_listed_pairs(lv, b)
+    _, ref, zero = oracle.forces(b.pos % b.L, b.mass, b.L, b.r_s, b.r_c)
+    np.testing.assert_array_equal(counts, ref[lv.perm])
+
+
+def test_coincident_particles_split_into_chunks():
+    pos = np.vstack([np.full((100, 3), 3.0), np.random.default_rng(1).random((50, 3)) * 20])
+    r_s, r_c = synth.box_params(20.0, 8)
+    b = synth.Box(pos=pos, mass=np.ones(150), L=20.0, n_pm=8, r_s=r_s, r_c=r_c)
+    lv = _build(b, 32)
+    A = lv.host_arrays()
+    assert A["leaf"][:, 1].max() <= 32
+    counts = _count_listed_pairs(lv, b)
+    _, ref, zero = oracle.forces(pos, b.mass, b.L, r_s, r_c)
+    np.testing.assert_array_equal(counts, ref[lv.perm])
+    assert zero.sum() == 100 * 99
+
+
+def test_leaf_offsets_are_exact_integers():
+    b = _clustered()
+    lv = _build(b, 8)
+    A = lv.host_arrays()
+    lc = A["lcen"][:, :3].astype(np.int64)
+    ent = A["pairs"]
+    I = np.repeat(np.arange(lc.shape[0]), np.diff(A["rowptr"]))
+    J = (ent >> 5).astype(np.int64)
+    code = (ent & 31).astype(np.int64)
+    nv = np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], 1)
+    diff = lc[J] - lc[I] + nv * 2 ** 22
+    assert np.abs(diff).max() < 2 ** 24  # exact in FP32
+    unit = b.L / 2.0 ** 22
+    np.testing.assert_allclose(diff * unit, lc[J] * unit + nv * b.L - lc[I] * unit, atol=1e-9)
+
+
+def test_schedule_largest_first():
+    b = _clustered()
+    lv = _build(b, 32)
+    A = lv.host_arrays()
+    items = A["items"]
+    assert np.array_equal(np.sort(items), np.arange(A["leaf"].shape[0]))
+    leaf, rowptr, pairs = A["leaf"], A["rowptr"], A["pairs"]
+    src = np.array([leaf[(pairs[rowptr[i]:rowptr[i + 1]] >> 5).astype(np.int64), 1].sum()
+                    for i in range(leaf.shape[0])])
+    cost = src * leaf[:, 1]
+    assert np.all(np.diff(cost[items]) <= 0)
+    assert lv.evaluated_pairs == cost.sum()
+
+
+def test_batch_keeps_boxes_apart():
+    boxes = [CASES["uniform"](), _clustered(n=1500), _small_box()]
+    lv = psr.Leaves.build_batch([(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G) for b in boxes],
+                                max_leaf=16)
+    A = lv.host_arrays()
+    nb = [b.n for b in boxes]
+    first = np.concatenate([[0], np.cumsum(nb)])
+    perm = lv.perm
+    leaf = A["leaf"]
+    for k in range(3):  # each box's particles stay in its own contiguous range
+        sl = slice(first[k], first[k + 1])
+        assert np.all((perm[sl] >= first[k]) & (perm[sl] < first[k + 1]))
+    box_of_leaf = leaf[:, 2]
+    I = np.repeat(np.arange(leaf.shape[0]), np.diff(A["rowptr"]))
+    J = (A["pairs"] >> 5).astype(np.int64)
+    assert np.all(box_of_leaf[I] == box_of_leaf[J])
+    assert lv.info.nbox == 3
+
+
+def test_argument_errors():
+    b = synth.small(nside=8)
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.L * 1.01, 1.0)
+    assert e.value.code == capi.PSR_E_CUTOFF
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.L, 1.0)
+    assert e.value.code == capi.PSR_E_CUTOFF
+    bad = b.pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.build(bad, b.mass, b.L, b.r_s, b.r_c)
+    assert e.value.code == capi.PSR_E_ARG
+    for ml in (0, 65):
+        with pytest.raises(capi.PsrError) as e:
+            psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, max_leaf=ml)
+        assert e.value.code == capi.PSR_E_ARG
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.build_batch([(b.pos, b.mass, b.L, b.r_s, b.r_c, 1.0),
+                                (b.pos, b.mass, b.L, b.r_s, 0.9 * b.r_c, 1.0)])
+    assert e.value.code == capi.PSR_E_ARG
+
+
+def test_positions_outside_box_are_wrapped():
+    b = synth.small(nside=8)
+    shifted = b.pos + np.array([3 * b.L, -2 * b.L, b.L])
+    lv0, lv1 = _build(b), psr.Leaves.build(shifted, b.mass, b.L, b.r_s, b.r_c)
+    a0, a1 = lv0.host_arrays(), lv1.host_arrays()
+    np.testing.assert_allclose(a1["pd"], a0["pd"], rtol=0, atol=1e-12 * b.L)
+    np.testing.assert_array_equal(a1["pairs"], a0["pairs"])
+
+
+def test_device_calls_refuse_before_upload():
+    b = synth.small(nside=8)
+    lv = _build(b)
+    with pytest.raises(capi.PsrError) as e:
+        lv.forces()
+    assert e.value.code == capi.PSR_E_STATE

@@ -1,0 +1,307 @@
+"""GPU parity: libpsr's kernels, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (relative RMS over all compared particles,
+sqrt(sum |da|^2 / sum |a|^2)):
+  FP64 path                   1e-6   (spec bound; observed ~1e-14)
+  FP32 paths vs exact oracle  2e-5   (spec bound)
+  FP32 table vs the oracle's interpolated T of the same table: 2e-6 (what
+  remains is FP32 rounding of coordinates and sums)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+psr = pytest.importorskip("paper_2107_14008_gb300")
+from paper_2107_14008_gb300 import capi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_14008_gb300 import build
+    build.build()
+
+
+def rel_rms(a, ref):
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.sqrt(np.sum((a - ref) ** 2) / max(np.sum(ref ** 2), 1e-300)))
+
+
+def _clustered(n=6000, L=60.0, seed=3, n_pm=16, halos=6):
+    rng = np.random.default_rng(seed)
+    pos, _ = synth.nfw_clustered(n, L, 0.6, halos, rng)
+    r_s, r_c = synth.box_params(L, n_pm)
+    return synth.Box(pos=pos, mass=rng.uniform(0.2, 2.0, n), L=L, n_pm=n_pm, r_s=r_s, r_c=r_c)
+
+
+def _small_box():
+    rng = np.random.default_rng(4)
+    L, n = 10.0, 500
+    r_s, r_c = synth.box_params(L, 8)
+    return synth.Box(pos=rng.random((n, 3)) * L, mass=rng.uniform(0.5, 1.5, n), L=L, n_pm=8,
+                     r_s=r_s, r_c=r_c)
+
+
+CASES = {
+    "uniform": lambda: synth.small(nside=20),
+    "clustered": _clustered,
+    "small_box": _small_box,
+}
+
+_oracle_cache = {}
+
+
+def oracle_acc(b, key, t_mode=oracle.T_EXACT, table_n=1024):
+    k = (key, t_mode, table_n)
+    if k not in _oracle_cache:
+        _oracle_cache[k] = oracle.forces(b.pos % b.L, b.mass, b.L, b.r_s, b.r_c, b.G,
+                                         t_mode=t_mode, table_n=table_n, cells=True)
+    return _oracle_cache[k]
+
+
+def gpu_forces(b, opts, max_leaf=32):
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
+    acc = lv.forces(opts)
+    lv.check()
+    return acc.double().cpu().numpy(), lv
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("max_leaf", [1, 8, 32, 64])
+def test_fp64_path_matches_oracle(case, max_leaf):
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case)
+    acc, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP64), max_leaf)
+    assert rel_rms(acc, ref) < 1e-6
+    np.testing.assert_allclose(acc, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+FP32_VARIANTS = [
+    ("exact", dict(precision=psr.PSR_FP32_EXACT)),
+    ("lin1024", dict(precision=psr.PSR_FP32_TABLE, table_n=1024, interp=psr.PSR_LINEAR)),
+    ("lin4096", dict(precision=psr.PSR_FP32_TABLE, table_n=4096, interp=psr.PSR_LINEAR)),
+    ("cub1024", dict(precision=psr.PSR_FP32_TABLE, table_n=1024, interp=psr.PSR_CUBIC)),
+    ("cub4096", dict(precision=psr.PSR_FP32_TABLE, table_n=4096, interp=psr.PSR_CUBIC)),
+]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("name,kw", FP32_VARIANTS)
+@pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
+def test_fp32_paths_match_oracle(case, name, kw, accum):
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case)
+    acc, _ = gpu_forces(b, psr.Options(accum=accum, **kw), 32)
+    assert rel_rms(acc, ref) < 2e-5, name
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered"])
+@pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
+                                         (psr.PSR_CUBIC, oracle.T_CUBIC)])
+@pytest.mark.parametrize("table_n", [256, 1024])
+def test_table_path_matches_interpolated_oracle(case, interp, mode, table_n):
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case, mode, table_n)
+    acc, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP32_TABLE, table_n=table_n,
+                                       interp=interp), 16)
+    assert rel_rms(acc, ref) < 2e-6
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_FP32_TABLE, psr.PSR_FP32_EXACT])
+def test_pair_count_matches_oracle(case, precision):
+    b = CASES[case]()
+    _, pairs, _ = oracle_acc(b, case)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=16).upload()
+    lv.forces(psr.Options(precision=precision, count_pairs=True))
+    got = lv.pair_count()
+    # FP32 distances can move a pair within one rounding of r_c across it
+    tol = 0 if precision == psr.PSR_FP64 else max(2, int(1e-6 * pairs.sum()))
+    assert abs(got - int(pairs.sum())) <= tol
+
+
+@pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
+                                         (psr.PSR_CUBIC, oracle.T_CUBIC)])
+@pytest.mark.parametrize("table_n", [64, 1024, 4096])
+def test_table_kernel_values(interp, mode, table_n):
+    x_c = 2.25
+    out = torch.zeros((table_n + 1, 4), dtype=torch.float32, device="cuda")
+    capi.psr_table(table_n, interp, x_c, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    tab = out.double().cpu().numpy()
+    assert np.all(tab[table_n] == 0.0)
+    h = x_c / table_n
+    x = np.linspace(0, x_c * (1 - 1e-9), 20011)
+    k = np.minimum(np.floor(x / h).astype(int), table_n - 1)
+    f = (x - k * h) / h - 0.5
+    c = tab[k]
+    if interp == psr.PSR_LINEAR:
+        val = c[:, 0] + f * c[:, 1]
+    else:
+        val = c[:, 0] + f * (c[:, 1] + f * (c[:, 2] + f * c[:, 3]))
+    ref = oracle.T(x, mode, table_n, x_c)
+    assert np.max(np.abs(val - ref)) < 4e-7  # FP32 rounding of the coefficients
+
+
+def test_isolated_pair_and_single_particle():
+    L = 100.0
+    r_s, r_c = 3.0, 13.5
+    d = np.array([2.0, -1.0, 0.5])
+    pos = np.array([[50.0, 50.0, 50.0], [50.0, 50.0, 50.0] + d])
+    m = np.array([0.7, 0.3])
+    ref, _, _ = oracle.forces(pos, m, L, r_s, r_c)
+    for prec in (psr.PSR_FP64, psr.PSR_FP32_EXACT, psr.PSR_FP32_TABLE):
+        lv = psr.Leaves.build(pos, m, L, r_s, r_c).upload()
+        acc = lv.forces(psr.Options(precision=prec)).double().cpu().numpy()
+        tol = 1e-12 if prec == psr.PSR_FP64 else 1e-6
+        np.testing.assert_allclose(acc, ref, rtol=tol)
+    one = psr.Leaves.build(pos[:1], m[:1], L, r_s, r_c).upload()
+    for prec in (psr.PSR_FP64, psr.PSR_FP32_TABLE):
+        assert np.all(one.forces(psr.Options(precision=prec)).cpu().numpy() == 0.0)
+
+
+def test_coincident_particles_give_finite_forces():
+    pos = np.vstack([np.full((70, 3), 3.0), np.random.default_rng(1).random((50, 3)) * 20])
+    m = np.ones(120)
+    r_s, r_c = synth.box_params(20.0, 8)
+    ref, _, _ = oracle.forces(pos, m, 20.0, r_s, r_c)
+    for prec in (psr.PSR_FP64, psr.PSR_FP32_TABLE, psr.PSR_FP32_EXACT):
+        lv = psr.Leaves.build(pos, m, 20.0, r_s, r_c).upload()
+        acc = lv.forces(psr.Options(precision=prec)).double().cpu().numpy()
+        assert np.all(np.isfinite(acc))
+        assert rel_rms(acc, ref) < (1e-9 if prec == psr.PSR_FP64 else 2e-5)
+
+
+def test_deterministic_and_batch_equals_single_boxes():
+    boxes = [synth.small(nside=12), _clustered(n=3000), _small_box()]
+    opts = psr.Options(precision=psr.PSR_FP32_TABLE)
+    lv = psr.Leaves.build_batch([(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G) for b in boxes],
+                                max_leaf=32).upload()
+    a1 = lv.forces(opts).cpu().numpy()
+    a2 = lv.forces(opts).cpu().numpy()
+    np.testing.assert_array_equal(a1, a2)
+    off = 0
+    for b in boxes:
+        single, _ = gpu_forces(b, opts, 32)
+        np.testing.assert_array_equal(a1[off:off + b.n], single.astype(np.float32))
+        off += b.n
+
+
+def test_cuda_graph_replay_matches_eager():
+    b = _clustered()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    opts = psr.Options(precision=psr.PSR_FP32_TABLE)
+    eager = lv.forces(opts).clone()
+    out = torch.zeros_like(eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lv.forces(opts, out=out)  # warm-up (builds nothing new)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lv.forces(opts, out=out)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager)
+    lv.check()
+
+
+def test_small_workload_all_targets():
+    """32^3 uniform, L=100, N_PM=32: every particle against the oracle."""
+    b = synth.small()
+    ref, _, _ = oracle.forces(b.pos, b.mass, b.L, b.r_s, b.r_c, cells=True)
+    acc64, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP64))
+    assert rel_rms(acc64, ref) < 1e-6
+    acc32, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP32_TABLE))
+    assert rel_rms(acc32, ref) < 2e-5
+
+
+@pytest.fixture(scope="module")
+def precision_workload():
+    b = synth.precision()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32).upload()
+    rng = np.random.default_rng(777)
+    tg = np.sort(rng.choice(b.n, 2000, replace=False))
+    ref, _, _ = oracle.forces(b.pos, b.mass, b.L, b.r_s, b.r_c, targets=tg, cells=True)
+    return b, lv, tg, ref
+
+
+@pytest.mark.parametrize("name,kw", FP32_VARIANTS)
+def test_precision_workload_sampled(precision_workload, name, kw):
+    """128^3 NFW (60 % in 4000 halos), L=500: 2000 sampled targets, the full
+    launch the benchmark times."""
+    b, lv, tg, ref = precision_workload
+    acc = lv.forces(psr.Options(**kw)).double().cpu().numpy()
+    lv.check()
+    assert np.all(np.isfinite(acc))
+    assert rel_rms(acc[tg], ref) < 2e-5, name
+
+
+def test_precision_workload_fp64_sampled(precision_workload):
+    b, lv, tg, ref = precision_workload
+    acc = lv.forces(psr.Options(precision=psr.PSR_FP64)).cpu().numpy()
+    assert rel_rms(acc[tg], ref) < 1e-6
+
+
+# ------------------------------------------------------------------ adjoint --
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "small_box"])
+def test_adjoint_fp64_matches_oracle(case):
+    b = CASES[case]()
+    cot = synth.cotangent(b.n, 5)
+    gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(precision=psr.PSR_FP64))
+    lv.check()
+    assert rel_rms(gx.cpu().numpy(), gx_ref) < 1e-6
+    assert rel_rms(gm.cpu().numpy(), gm_ref) < 1e-6
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "small_box"])
+@pytest.mark.parametrize("name,kw", FP32_VARIANTS)
+def test_adjoint_fp32_matches_oracle(case, name, kw):
+    b = CASES[case]()
+    cot = synth.cotangent(b.n, 5)
+    gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(**kw))
+    lv.check()
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4, name
+    assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
+
+
+def test_adjoint_fp64_matches_finite_differences():
+    b = _clustered(n=4000, L=40.0, seed=5)
+    cot = synth.cotangent(b.n, 99)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(precision=psr.PSR_FP64))
+    gx, gm = gx.cpu().numpy(), gm.cpu().numpy()
+    tg = np.arange(0, b.n, 41)
+    fx = np.array([oracle.fd_gradient(b.pos % b.L, b.mass, cot, p, b.L, b.r_s, b.r_c,
+                                      richardson=True)[0] for p in tg])
+    assert rel_rms(gx[tg], fx) < 1e-5
+
+
+def test_autograd_function_backward_is_adjoint():
+    b = _clustered(n=2000)
+    pos = torch.tensor(b.pos, device="cuda", requires_grad=True)
+    mass = torch.tensor(b.mass, device="cuda", requires_grad=True)
+    opts = psr.Options(precision=psr.PSR_FP64)
+    acc = psr.forces(pos, mass, b.L, b.r_s, b.r_c, b.G, opts)
+    cot = torch.tensor(synth.cotangent(b.n, 3), device="cuda")
+    (acc * cot).sum().backward()
+    gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot.cpu().numpy(), b.L, b.r_s, b.r_c,
+                                    b.G, cells=True)
+    assert rel_rms(pos.grad.cpu().numpy(), gx_ref) < 1e-6
+    assert rel_rms(mass.grad.cpu().numpy(), gm_ref) < 1e-6
