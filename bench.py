@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_INTERACTION = 51  # paper, Section 5
+METRIC = "G pair-interactions/s & % FP32 peak, FP32-table vs FP64 path, at stated force err"
 
 
 def parse():
@@ -46,7 +47,9 @@ def parse():
     p.add_argument("--cpu-targets", type=int, default=100000,
                    help="targets in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--nside", type=int, default=128)
+    p.add_argument("--workload", default="precision", choices=["precision", "adjoint64"],
+                   help="precision: 128^3 NFW, L=500 (the headline); adjoint64: 64^3 NFW, L=200 "
+                        "(a small case of the same kernels for profiling)")
     return p.parse_args()
 
 
@@ -146,8 +149,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import synth
-    b = synth.precision(nside=args.nside)
+    b = make_box(args)
     vals = []
     for _ in range(args.warmup):
         cpu_baseline(b, None, max(1000, args.cpu_targets // 20))
@@ -157,11 +159,13 @@ def run_reference(args):
     pairs = sum(v["pairs"] for v in vals)
     secs = sum(v["seconds"] for v in vals)
     value = pairs / secs / 1e9
-    line = {"impl": "reference", "metric": "pair-interactions/s (FP64 CPU oracle)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "G pair-interactions/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(b, args),
+            "data": "synthetic",
+            "config": dict(workload_config(b, args),
+                           path="FP64 CPU oracle (cell list), within-cutoff pairs counted"),
             "cpu_baseline": {"value": value, "unit": "G pair-interactions/s",
                              "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": "each step: %d random targets against all sources"
@@ -171,9 +175,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def make_box(args, rank=0):
+    import synth
+    if args.workload == "adjoint64":
+        return synth.adjoint(seed=12348 + rank)
+    return synth.precision(seed=12346 + rank)
+
+
 def workload_config(b, args):
-    return {"workload": "NFW-clustered %d^3, L=%g, N_PM=%d, 60%% mass in 4000 halos, "
-                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=32" % (args.nside, b.L, b.n_pm),
+    return {"workload": "NFW-clustered %d^3, L=%g, N_PM=%d, 60%% mass in %d halos, "
+                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=32"
+                        % (b.n_pm, b.L, b.n_pm, b.meta.get("n_halos", 0)),
             "n": b.n, "L": b.L, "r_s": b.r_s, "r_c": b.r_c, "max_leaf": 32,
             "path": "FP32 pair math, T from a %d-interval %s table in shared memory, %s "
                     "accumulation" % (args.table_n, args.interp, args.accum),
@@ -185,7 +197,6 @@ def run_psr(args):
     import torch
 
     import paper_2107_14008_gb300 as psr
-    import synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -195,7 +206,7 @@ def run_psr(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    b = synth.precision(seed=12346 + rank, nside=args.nside)
+    b = make_box(args, rank)
     t0 = time.perf_counter()
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
     build_s = time.perf_counter() - t0
@@ -295,7 +306,7 @@ def run_psr(args):
     achieved = FLOPS_PER_INTERACTION * evaluated / (mean_ms / 1e3) / 1e12
     clocks = clk.summary()
     line = {
-        "metric": "G pair-interactions/s & % FP32 peak, FP32-table vs FP64 path, at stated force err",
+        "metric": METRIC,
         "value": value, "unit": "G pair-interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": mean_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
