@@ -63,6 +63,11 @@ extern "C" {
 /* interpolation of the table (PSR_FP32_TABLE) */
 #define PSR_LINEAR 0      /* chord between nodes                            */
 #define PSR_CUBIC 1       /* cubic Hermite on (T_k, T'_k = x_k^2 E_k)       */
+/* inner loop of the FP32 forward kernels */
+#define PSR_KERNEL_AUTO 0   /* the library's default (scalar streams)          */
+#define PSR_KERNEL_SCALAR 1 /* one source particle per lane and iteration      */
+#define PSR_KERNEL_PACKED 2 /* two source particles per lane and iteration in
+                               packed f32x2 arithmetic (sm_100+)               */
 /* accumulation of FP32 partial sums across source leaves */
 #define PSR_ACC_FP64 0    /* fold into FP64 accumulators                    */
 #define PSR_ACC_KAHAN32 1 /* fold with compensated (two-sum) FP32           */
@@ -80,12 +85,13 @@ typedef struct {
                             [64, 8192]; 0 = 1024                              */
     int interp;          /* PSR_LINEAR | PSR_CUBIC                            */
     int accum;           /* PSR_ACC_FP64 | PSR_ACC_KAHAN32                    */
-    int warps_per_block; /* 0 = default (8)                                   */
+    int warps_per_block; /* 1..8; 0 = default (8)                            */
     int blocks_per_sm;   /* 0 = default (occupancy-derived)                   */
     int fold_every;      /* source particles summed in FP32 before a fold;
                             0 = default (64)                                  */
     int count_pairs;     /* 1: also count pairs with 0 < r < r_c (slower)     */
-    int reserved[8];     /* must be zero                                      */
+    int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED (FP32 forward) */
+    int reserved[7];     /* must be zero                                      */
 } psr_opts;
 
 typedef struct {

@@ -13,10 +13,12 @@ import numpy as np
 
 from . import capi
 from .capi import (PSR_ACC_FP64, PSR_ACC_KAHAN32, PSR_CUBIC, PSR_FP32_EXACT, PSR_FP32_TABLE,
-                   PSR_FP64, PSR_LINEAR, PsrError)
+                   PSR_FP64, PSR_KERNEL_AUTO, PSR_KERNEL_PACKED, PSR_KERNEL_SCALAR, PSR_LINEAR,
+                   PsrError)
 
 __all__ = ["Options", "Leaves", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
-           "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_ACC_FP64", "PSR_ACC_KAHAN32"]
+           "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_ACC_FP64", "PSR_ACC_KAHAN32",
+           "PSR_KERNEL_AUTO", "PSR_KERNEL_SCALAR", "PSR_KERNEL_PACKED"]
 
 
 @dataclass
@@ -30,6 +32,7 @@ class Options:
     blocks_per_sm: int = 0
     fold_every: int = 0
     count_pairs: bool = False
+    kernel: int = 0
 
     def c(self):
         o = capi.psr_opts()
@@ -37,6 +40,7 @@ class Options:
                                                      int(self.interp), int(self.accum))
         o.warps_per_block, o.blocks_per_sm = int(self.warps_per_block), int(self.blocks_per_sm)
         o.fold_every, o.count_pairs = int(self.fold_every), int(bool(self.count_pairs))
+        o.kernel = int(self.kernel)
         return o
 
     @property

@@ -11,8 +11,8 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+SRC = os.environ.get("PSR_SRC_DIR") or os.path.join(HERE, "csrc")
+OUT = os.environ.get("PSR_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsr.so")
 ROOT = os.path.dirname(HERE)
 
@@ -22,7 +22,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--ftz=tr
               "-I" + os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function",
              "-I" + os.path.join(ROOT, "include")]
-CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f64.cu", "p2p_adj.cu", "capi.cu"]
+CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_f64.cu",
+              "p2p_adj.cu", "capi.cu"]
 CXX_SOURCES = ["builder.cpp"]
 
 
@@ -55,7 +56,8 @@ def build(force=False, verbose=False):
         src = os.path.join(SRC, f)
         obj = os.path.join(OUT, f + ".o")
         if force or _needs(obj, [src] + hdrs):
-            jobs.append(([nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj], obj))
+            extra = os.environ.get("PSR_NVCC_EXTRA", "").split()
+            jobs.append(([nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj], obj))
     for f in CXX_SOURCES:
         src = os.path.join(SRC, f)
         obj = os.path.join(OUT, f + ".o")

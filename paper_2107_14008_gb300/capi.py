@@ -8,7 +8,7 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpsr.so")
+LIB_PATH = os.environ.get("PSR_LIB") or os.path.join(HERE, "_build", "libpsr.so")
 
 PSR_OK = 0
 PSR_E_ARG, PSR_E_CUTOFF, PSR_E_WORKSPACE, PSR_E_CUDA = -1, -2, -3, -4
@@ -16,6 +16,7 @@ PSR_E_DEVICE, PSR_E_TIMEOUT, PSR_E_NOMEM, PSR_E_STATE = -5, -6, -7, -8
 PSR_FP64, PSR_FP32_EXACT, PSR_FP32_TABLE = 0, 1, 2
 PSR_LINEAR, PSR_CUBIC = 0, 1
 PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
+PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED = 0, 1, 2
 PSR_BUILD_NO_FP64 = 1
 
 # every symbol include/psr.h declares
@@ -33,7 +34,8 @@ class psr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("table_n", ctypes.c_int), ("interp", ctypes.c_int),
                 ("accum", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("fold_every", ctypes.c_int),
-                ("count_pairs", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("count_pairs", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class psr_info(ctypes.Structure):

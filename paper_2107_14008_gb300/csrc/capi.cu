@@ -43,7 +43,7 @@ int wait_stream(cudaStream_t st, int timeout_ms)
 }
 
 struct Opts {
-    int precision, table_n, interp, accum, warps, bps, fold, count;
+    int precision, table_n, interp, accum, warps, bps, fold, count, kernel;
 };
 
 int check_opts(const psr_opts* o, Opts* out)
@@ -51,8 +51,10 @@ int check_opts(const psr_opts* o, Opts* out)
     psr_opts d{};
     d.precision = PSR_FP32_TABLE;
     if (!o) o = &d;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) return fail(PSR_E_ARG, "psr_opts.reserved must be zero");
+    if (o->kernel < PSR_KERNEL_AUTO || o->kernel > PSR_KERNEL_PACKED)
+        return fail(PSR_E_ARG, "psr_opts.kernel out of range");
     if (o->precision < PSR_FP64 || o->precision > PSR_FP32_TABLE)
         return fail(PSR_E_ARG, "psr_opts.precision out of range");
     int tn = o->table_n ? o->table_n : 1024;
@@ -62,13 +64,33 @@ int check_opts(const psr_opts* o, Opts* out)
         return fail(PSR_E_ARG, "psr_opts.interp out of range");
     if (o->accum != PSR_ACC_FP64 && o->accum != PSR_ACC_KAHAN32)
         return fail(PSR_E_ARG, "psr_opts.accum out of range");
-    int w = o->warps_per_block ? o->warps_per_block : 8;
-    if (w < 1 || w > 8) return fail(PSR_E_ARG, "psr_opts.warps_per_block must be in [1, 8]");
+    int w = o->warps_per_block;
+    if (w < 0 || w > 32) return fail(PSR_E_ARG, "psr_opts.warps_per_block must be in [0, 32]");
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64)
         return fail(PSR_E_ARG, "psr_opts.blocks_per_sm must be in [0, 64]");
     int fold = o->fold_every ? o->fold_every : 64;
     if (fold < 1) return fail(PSR_E_ARG, "psr_opts.fold_every must be positive");
-    *out = Opts{o->precision, tn, o->interp, o->accum, w, o->blocks_per_sm, fold, o->count_pairs ? 1 : 0};
+    *out = Opts{o->precision, tn, o->interp, o->accum, w, o->blocks_per_sm, fold,
+                o->count_pairs ? 1 : 0, o->kernel == PSR_KERNEL_AUTO ? PSR_KERNEL_SCALAR : o->kernel};
+    return PSR_OK;
+}
+
+// Warps per block: every kernel is built for at most 256 threads (8 warps).
+int resolve_warps(Opts& o, bool fwd32)
+{
+    (void)fwd32;
+    if (o.warps == 0) o.warps = 8;
+    if (o.warps > 8) return fail(PSR_E_ARG, "warps_per_block must be in [1, 8]");
+    return PSR_OK;
+}
+
+// Staging capacity per warp; the table and the staging buffers must fit in one
+// block's shared memory.
+int fwd32_smem_config(const Opts& o, int* cap)
+{
+    *cap = 256;
+    if (fwd_f32_smem(o.precision, o.interp, o.table_n, o.warps, *cap) > kSmemPerBlock)
+        return fail(PSR_E_ARG, "table and staging buffers exceed shared memory; use fewer warps");
     return PSR_OK;
 }
 
@@ -101,6 +123,7 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     a.count_pairs = o.count;
     a.warps_per_block = o.warps;
     a.max_leaf = h->max_leaf;
+    a.variant = o.kernel;
     return a;
 }
 
@@ -127,8 +150,12 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
             e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n, &occ);
         else if (o.precision == PSR_FP64)
             e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
-        else
-            e = fwd_f32_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n, &occ);
+        else {
+            int cap;
+            if ((e = fwd32_smem_config(o, &cap))) return e;
+            e = fwd_f32_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
+                                  cap, o.kernel, &occ);
+        }
         if (e) return cuda_fail((cudaError_t)e, "occupancy query");
         bps = occ > 0 ? occ : 1;
     }
@@ -245,9 +272,12 @@ int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stre
     if (o.precision == PSR_FP64 && h->pd.empty())
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     cudaStream_t st = (cudaStream_t)stream;
+    const bool fwd32 = o.precision != PSR_FP64;
+    if ((rc = resolve_warps(o, fwd32))) return rc;
     if ((rc = ensure_table(h, o, st))) return rc;
     FwdArgs a = base_args(h, o);
     a.out = d_acc;
+    if (fwd32 && (rc = fwd32_smem_config(o, &a.stage_cap))) return rc;
     if ((rc = grid_blocks(h, o, 0, &a.blocks))) return rc;
     if (o.count) {
         cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 8, st);
@@ -272,6 +302,7 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     if (o.precision == PSR_FP32_TABLE && o.interp == PSR_CUBIC && o.table_n > 4096)
         return fail(PSR_E_ARG, "cubic adjoint tables hold at most 4096 intervals (shared memory)");
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = resolve_warps(o, false))) return rc;
     if ((rc = ensure_table(h, o, st))) return rc;
     FwdArgs a = base_args(h, o);
     a.cot = d_cot;

@@ -1,0 +1,570 @@
+// FP32 forward P2P kernels (paper, Section 3.2, Algorithms 1 and 2, redesigned
+// for sm_103a): shared device code of the two kernel variants.
+//
+// Work decomposition.  The paper gives one thread block to each target leaf
+// and one thread to each target particle, with the j-leaf staged in shared
+// memory.  Leaves here hold 1-64 particles (mean ~9 on clustered sets), so one
+// WARP takes one target leaf: each lane holds R = 1 or 2 target particles, the
+// n_I targets occupy T = ceil(n_I / R) lanes, and the warp's 32 lanes form
+// S = 32 / T streams.  The row's source leaves are staged chunk by chunk into a
+// per-warp shared-memory buffer, already shifted into the target leaf's frame,
+// and stream s takes staged particles s, s+S, ... (one broadcast shared-memory
+// load serves the T lanes of a stream).  Two variants of the inner loop:
+// scalar streams (one source per iteration) and packed pairs (two sources per
+// iteration in sm_100+ f32x2 arithmetic, half the issue slots per pair).  The
+// S partial sums of each target are combined through shared memory at the end.  Warps take target leaves
+// from an atomic ticket in largest-work-first order (persistent grid, no
+// inter-block waits).
+//
+// Precision.  Pair arithmetic is FP32 in leaf-local coordinates scaled by
+// 1/(2 r_s); the offset between two leaf centres (with the periodic image) is
+// an exact integer in units of L/2^22, converted to FP32 once per leaf pair.
+// FP32 partial sums over one staged chunk (<= 256 source particles) are folded
+// into FP64 (PSR_ACC_FP64) or compensated FP32 (PSR_ACC_KAHAN32) accumulators.
+//
+// T(x).  Exact: erfcf + expf.  Table: T on [0, x_c] with N intervals, held in
+// shared memory: linear (midpoint value, chord difference) or cubic Hermite
+// (monomial coefficients about the midpoint); index N is a zero sentinel, so
+// the cutoff (x >= x_c) costs no extra instruction.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kcommon.cuh"
+
+namespace psr {
+
+enum { TM_EXACT = 0, TM_LINEAR = 1, TM_CUBIC = 2 };
+
+// exact T(x) with the hard cutoff
+__device__ __forceinline__ float eval_T_exact(float x, float x_c)
+{
+    float T = erfcf(x) + kTwoOverSqrtPi * x * expf(-x * x);
+    return x < x_c ? T : 0.0f;
+}
+
+template <int ACC>
+struct Acc3 {
+    double x = 0, y = 0, z = 0;  // FP64 mode
+    float sx = 0, sy = 0, sz = 0, cx = 0, cy = 0, cz = 0;  // Kahan mode
+    __device__ __forceinline__ void fold(float& fx, float& fy, float& fz)
+    {
+        if (ACC == PSR_ACC_FP64) {
+            x += (double)fx;
+            y += (double)fy;
+            z += (double)fz;
+        } else {
+            float s, e;
+            two_sum(sx, fx, s, e); sx = s; cx += e;
+            two_sum(sy, fy, s, e); sy = s; cy += e;
+            two_sum(sz, fz, s, e); sz = s; cz += e;
+        }
+        fx = fy = fz = 0.0f;
+    }
+};
+
+// Per-warp shared-memory staging of a row's source particles.  Up to 32 row
+// entries are examined at once (lane k reads entry e0 + k); a warp prefix sum
+// of their leaf sizes gives each leaf's slot in the buffer, and as many whole
+// leaves as fit in `cap` slots are taken.  Each staged particle is written
+// already shifted into the target leaf's frame (its leaf offset added), so the
+// compute loop that follows is uniform over the chunk.
+constexpr int kMetaPerWarp = 32; // entries per chunk (one per lane)
+
+// Stages one chunk starting at entry e0; returns the number of entries taken
+// and sets nst to the number of staged particles.  Staged coordinates are
+// multiplied by sc (the kernels' working unit per FP32 coordinate unit).
+// PK = false: one float4 (x, y, z, m) per particle; PK = true: particle pairs
+// interleaved for packed arithmetic, an odd count padded with a massless
+// particle far beyond the cutoff.
+template <bool PK>
+__device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long long re,
+                                           int4 ci, float unit, float sc, int cap,
+                                           float4* __restrict__ stage,
+                                           float4* __restrict__ meta, int& nst)
+{
+    const int lane = threadIdx.x & 31;
+    const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
+    const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
+    const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
+    const long long e = e0 + lane;
+    int cnt = 0, first = 0;
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    if (e < re) {
+        unsigned ent = a.pairs[e];
+        int J = (int)(ent >> 5);
+        unsigned code = ent & 31u;
+        bool ok = J < a.n_leaves && code < (unsigned)kShiftCodes;
+        int4 lj = make_int4(0, 0, 0, 0);
+        if (ok) {
+            lj = leaf[J];
+            ok = lj.x >= 0 && lj.y >= 1 && lj.y <= a.max_leaf && (long long)lj.x + lj.y <= a.n;
+        }
+        if (ok) {
+            int4 cj = lcen[J];
+            int nx, ny, nz;
+            decode_shift(code, nx, ny, nz);
+            ox = (float)(cj.x - ci.x + nx * (1 << kCentreShift)) * unit;
+            oy = (float)(cj.y - ci.y + ny * (1 << kCentreShift)) * unit;
+            oz = (float)(cj.z - ci.z + nz * (1 << kCentreShift)) * unit;
+            cnt = lj.y;
+            first = lj.x;
+        } else {
+            // a bad entry becomes one particle placed far beyond the cutoff
+            set_error(a.ctrl, kErrLeafIndex);
+            cnt = 1;
+            first = 0;
+            ox = oy = oz = 1e18f;
+        }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned fit = __ballot_sync(kFull, e < re && incl <= cap);
+    const int ntake = __popc(fit);  // >= 1: one leaf always fits
+    nst = __shfl_sync(kFull, incl, ntake - 1);
+    const int excl = incl - cnt;
+    if (lane < ntake)
+        meta[lane] = make_float4(__int_as_float(first - excl), ox * sc, oy * sc, oz * sc);
+    __syncwarp();
+    // slot p belongs to the entry k with excl_k <= p < excl_{k+1}: count the
+    // entry starts at or before p with a position bitmask per 32-slot round
+    int C = 0;
+    for (int p0 = 0; p0 < nst + (PK ? (nst & 1) : 0); p0 += 32) {
+        const int rel = excl - p0;
+        const unsigned bit = (lane < ntake && rel >= 0 && rel < 32) ? (1u << rel) : 0u;
+        const unsigned M = __reduce_or_sync(kFull, bit);
+        const int k = C + __popc(M & ((2u << lane) - 1u)) - 1;
+        C += __popc(M);
+        const int p = p0 + lane;
+        if (p < nst) {
+            const float4 m = meta[k];
+            const float4 v = __ldg(pf + (__float_as_int(m.x) + p));
+            if (PK) {
+                // pair j = p/2 occupies two float4: (x0, x1, y0, y1), (z0, z1, m0, m1)
+                float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + (p & 1);
+                d[0] = fmaf(v.x, sc, m.y);
+                d[2] = fmaf(v.y, sc, m.z);
+                d[4] = fmaf(v.z, sc, m.w);
+                d[6] = v.w;
+            } else {
+                stage[p] = make_float4(fmaf(v.x, sc, m.y), fmaf(v.y, sc, m.z), fmaf(v.z, sc, m.w), v.w);
+            }
+        } else if (PK && p == nst && (nst & 1)) {
+            // pad an odd chunk with a massless particle far beyond the cutoff
+            float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + 1;
+            d[0] = d[2] = d[4] = 1e18f;
+            d[6] = 0.0f;
+        }
+    }
+    __syncwarp();
+    return ntake;
+}
+
+// Combine the S stream partial sums of each target through shared memory
+// (the warp's staging buffer) and write the accelerations, scaled by gout, in
+// the original particle order.
+template <int ACC, int R>
+__device__ __forceinline__ void finish_item(const FwdArgs& a, int4 li, Acc3<ACC>* acc,
+                                            const bool* act, int lane, int s, int q, int S, int T,
+                                            float gout, float4* __restrict__ stage)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (ACC == PSR_ACC_FP64) {
+            double* red = reinterpret_cast<double*>(stage);
+            red[3 * lane + 0] = acc[r].x;
+            red[3 * lane + 1] = acc[r].y;
+            red[3 * lane + 2] = acc[r].z;
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                double sx = acc[r].x, sy = acc[r].y, sz = acc[r].z;
+                for (int t = 1; t < S; ++t) {
+                    sx += red[3 * (lane + t * T) + 0];
+                    sy += red[3 * (lane + t * T) + 1];
+                    sz += red[3 * (lane + t * T) + 2];
+                }
+                int idx = a.perm[li.x + q + T * r];
+                float* out = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                out[0] = (float)(sx * (double)gout);
+                out[1] = (float)(sy * (double)gout);
+                out[2] = (float)(sz * (double)gout);
+            }
+        } else {
+            float* red = reinterpret_cast<float*>(stage);
+            red[6 * lane + 0] = acc[r].sx;
+            red[6 * lane + 1] = acc[r].cx;
+            red[6 * lane + 2] = acc[r].sy;
+            red[6 * lane + 3] = acc[r].cy;
+            red[6 * lane + 4] = acc[r].sz;
+            red[6 * lane + 5] = acc[r].cz;
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                float sx = acc[r].sx, cx = acc[r].cx, sy = acc[r].sy, cy = acc[r].cy;
+                float sz = acc[r].sz, cz = acc[r].cz, u, v;
+                for (int t = 1; t < S; ++t) {
+                    const float* o = red + 6 * (lane + t * T);
+                    two_sum(sx, o[0], u, v); sx = u; cx += o[1] + v;
+                    two_sum(sy, o[2], u, v); sy = u; cy += o[3] + v;
+                    two_sum(sz, o[4], u, v); sz = u; cz += o[5] + v;
+                }
+                int idx = a.perm[li.x + q + T * r];
+                float* out = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                out[0] = (sx + cx) * gout;
+                out[1] = (sy + cy) * gout;
+                out[2] = (sz + cz) * gout;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Packed FP32 helpers (sm_100+ f32x2 instructions: two lanes of work per issue)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// T for a pair of table coordinates t = u - 1/2, u = x N / x_c (one FFMA of
+// r^2 and 1/r when coordinates are in table units).  Table entries: linear
+// (M_k, D_k) float2, cubic (c0..c3) float4, entry N = 0 (beyond the cutoff).
+// The index comes from the 1.5*2^23 rounding trick: the float bits of
+// t + 1.5*2^23 hold rint(t) in their low bits, so an entry address is one
+// multiply-add of them.
+template <int TM>
+__device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsigned tab_bias,
+                                          float nmax, float x_c, float xscale)
+{
+    if (TM == TM_EXACT) {
+        return make_float2(eval_T_exact(r2.x * rinv.x * xscale, x_c),
+                           eval_T_exact(r2.y * rinv.y * xscale, x_c));
+    } else {
+        t.x = fminf(t.x, nmax);
+        t.y = fminf(t.y, nmax);
+        const float2 fk = add2(t, make_float2(kMagic, kMagic));
+        const float2 kf = add2(fk, make_float2(-kMagic, -kMagic));
+        const float2 f = fma2(kf, make_float2(-1.0f, -1.0f), t);
+        const unsigned ka = (unsigned)__float_as_int(fk.x), kb = (unsigned)__float_as_int(fk.y);
+        if (TM == TM_LINEAR) {
+            const float2 ca = lds_f2(ka * 8u + tab_bias), cb = lds_f2(kb * 8u + tab_bias);
+            return make_float2(fmaf(f.x, ca.y, ca.x), fmaf(f.y, cb.y, cb.x));
+        } else {
+            const float4 ca = lds_f4(ka * 16u + tab_bias), cb = lds_f4(kb * 16u + tab_bias);
+            return make_float2(fmaf(f.x, fmaf(f.x, fmaf(f.x, ca.w, ca.z), ca.y), ca.x),
+                               fmaf(f.y, fmaf(f.y, fmaf(f.y, cb.w, cb.z), cb.y), cb.x));
+        }
+    }
+}
+
+// One target leaf on one warp.  R = targets per lane; T = ceil(n_I / R) lanes
+// per stream, S = 32 / T streams.  Each stream takes staged particle PAIRS
+// s, s+S, ... and evaluates both particles of a pair at once with packed
+// FP32 (f32x2) arithmetic.
+template <int TM, int ACC, bool COUNT, int R>
+__device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
+                                            float4* __restrict__ stage, float4* __restrict__ meta,
+                                         unsigned long long& npairs)
+{
+    const int lane = threadIdx.x & 31;
+    const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
+    const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
+    const int nI = li.y;
+    const int T = (nI + R - 1) / R;
+    const int S = 32 / T;
+    const int s = lane / T;
+    const int q = lane - s * T;
+    const bool on = s < S;
+    const BoxDev& bx = a.boxes[li.z];
+    const float x_c = bx.x_c;
+    const float nmax = (float)a.table_n;
+    // working unit: table intervals (u = x N / x_c) for the table path, x itself
+    // for the exact path
+    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    const float xscale = 1.0f / sc;  // working unit -> x (exact path only)
+    const float unit = bx.unit;
+    const int4 ci = lcen[I];
+
+    float2 ntx[R], nty[R], ntz[R];  // minus the target coordinates, both halves
+    bool act[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int t = q + T * r;
+        act[r] = on && t < nI;
+        const float4 v = pf[li.x + (act[r] ? t : 0)];
+        ntx[r] = make_float2(-v.x * sc, -v.x * sc);
+        nty[r] = make_float2(-v.y * sc, -v.y * sc);
+        ntz[r] = make_float2(-v.z * sc, -v.z * sc);
+    }
+    Acc3<ACC> acc[R];
+    float2 fx[R], fy[R], fz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) fx[r] = fy[r] = fz[r] = make_float2(0.0f, 0.0f);
+    unsigned cnt = 0;
+    const long long re = a.rowptr[I + 1];
+    long long e0 = a.rowptr[I];
+    const float eps = kEps2 * sc * sc;
+    const float2 eps2 = make_float2(eps, eps);
+    const float2 mhalf = make_float2(-0.5f, -0.5f);
+    while (e0 < re) {
+        int nst;
+        e0 += stage_chunk<true>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (on) {
+            const int npair = (nst + 1) >> 1;
+#pragma unroll 1
+            for (int k = s; k < npair; k += S) {
+                const float4 A = stage[2 * k];
+                const float4 B = stage[2 * k + 1];
+                const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
+                const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 dx = add2(px, ntx[r]), dy = add2(py, nty[r]), dz = add2(pz, ntz[r]);
+                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+                    const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+                    const float2 t = fma2(r2, rinv, mhalf);
+                    const float2 Tv = eval_T2<TM>(t, r2, rinv, tab_bias, nmax, x_c, xscale);
+                    const float2 w = mul2(mul2(mul2(mul2(pm, Tv), rinv), rinv), rinv);
+                    fx[r] = fma2(w, dx, fx[r]);
+                    fy[r] = fma2(w, dy, fy[r]);
+                    fz[r] = fma2(w, dz, fz[r]);
+                    if (COUNT) {
+                        const float uc = TM == TM_EXACT ? x_c : nmax;
+                        const float ua = r2.x * rinv.x, ub = r2.y * rinv.y;
+                        cnt += (act[r] && ua < uc && (dx.x != 0.0f || dy.x != 0.0f || dz.x != 0.0f));
+                        cnt += (act[r] && ub < uc && (dx.y != 0.0f || dy.y != 0.0f || dz.y != 0.0f));
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float sx = fx[r].x + fx[r].y, sy = fy[r].x + fy[r].y, sz = fz[r].x + fz[r].y;
+                acc[r].fold(sx, sy, sz);
+                fx[r] = fy[r] = fz[r] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncwarp();
+    }
+    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_acc * sc * sc, stage);
+    if (COUNT) npairs += cnt;
+}
+
+// T for one table coordinate t = u - 1/2 (see eval_T2).
+template <int TM>
+__device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned tab_bias,
+                                         float nmax, float x_c, float xscale)
+{
+    if (TM == TM_EXACT) return eval_T_exact(r2 * rinv * xscale, x_c);
+    t = fminf(t, nmax);
+    const float fk = t + kMagic;
+    const float f = t - (fk - kMagic);
+    const unsigned k = (unsigned)__float_as_int(fk);
+    if (TM == TM_LINEAR) {
+        const float2 c = lds_f2(k * 8u + tab_bias);
+        return fmaf(f, c.y, c.x);
+    } else {
+        const float4 c = lds_f4(k * 16u + tab_bias);
+        return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+    }
+}
+
+// Scalar-stream variant: stream s takes staged particles s, s+S, ... one at
+// a time (two iterations in flight per warp).
+template <int TM, int ACC, bool COUNT, int R>
+__device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
+                                            float4* __restrict__ stage,
+                                            float4* __restrict__ meta, unsigned long long& npairs)
+{
+    const int lane = threadIdx.x & 31;
+    const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
+    const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
+    const int nI = li.y;
+    const int T = (nI + R - 1) / R;
+    const int S = 32 / T;
+    const int s = lane / T;
+    const int q = lane - s * T;
+    const bool on = s < S;
+    const BoxDev& bx = a.boxes[li.z];
+    const float x_c = bx.x_c;
+    const float nmax = (float)a.table_n;
+    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    const float xscale = 1.0f / sc;
+    const float unit = bx.unit;
+    const int4 ci = lcen[I];
+
+    float4 xi[R];
+    bool act[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int t = q + T * r;
+        act[r] = on && t < nI;
+        xi[r] = pf[li.x + (act[r] ? t : 0)];
+        xi[r].x *= sc;
+        xi[r].y *= sc;
+        xi[r].z *= sc;
+    }
+    Acc3<ACC> acc[R];
+    float fx[R], fy[R], fz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) fx[r] = fy[r] = fz[r] = 0.0f;
+    unsigned cnt = 0;
+    const long long re = a.rowptr[I + 1];
+    long long e0 = a.rowptr[I];
+    const float eps2 = kEps2 * sc * sc;
+    while (e0 < re) {
+        int nst;
+        e0 += stage_chunk<false>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (on) {
+#pragma unroll 2
+            for (int k = s; k < nst; k += S) {
+                const float4 p = stage[k];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                    float rinv = rsqrt_ftz(r2);
+                    float Tv = eval_T1<TM>(fmaf(r2, rinv, -0.5f), r2, rinv, tab_bias, nmax, x_c,
+                                           xscale);
+                    float w = p.w * Tv * rinv * rinv * rinv;
+                    fx[r] = fmaf(w, dx, fx[r]);
+                    fy[r] = fmaf(w, dy, fy[r]);
+                    fz[r] = fmaf(w, dz, fz[r]);
+                    if (COUNT) {
+                        const float u = r2 * rinv;
+                        const float uc = TM == TM_EXACT ? x_c : nmax;
+                        cnt += (act[r] && u < uc && (dx != 0.0f || dy != 0.0f || dz != 0.0f));
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r].fold(fx[r], fy[r], fz[r]);
+        }
+        __syncwarp();
+    }
+    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_acc * sc * sc, stage);
+    if (COUNT) npairs += cnt;
+}
+
+// Lane-slot efficiency of R targets per lane: n_I * floor(32 / ceil(n_I/R)) / (32 R)
+__device__ __forceinline__ bool prefer_two_per_lane(int n)
+{
+    if (n > 32) return true;
+    int t2 = (n + 1) >> 1;
+    int e1 = n * (32 / n);          // x 1/32
+    int e2 = n * (32 / t2);         // x 1/64
+    return e2 > 2 * e1 + (2 * e1) / 16;  // > 6 % better
+}
+
+// Shared memory: the table, then one staging buffer of stage_cap particles
+// plus 32 entry records per warp.
+template <int TM, int ACC, bool COUNT, bool WIDE, bool PK>
+__global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const unsigned esize = TM == TM_CUBIC ? 16u : 8u;
+    const size_t tab_bytes = TM == TM_EXACT ? 0 : (size_t)(a.table_n + 1) * esize;
+    float4* stage = reinterpret_cast<float4*>(smem + ((tab_bytes + 15) & ~(size_t)15)) +
+                    (size_t)warp * (a.stage_cap + kMetaPerWarp);
+    float4* meta = stage + a.stage_cap;
+    if (TM != TM_EXACT) {
+        const float4* g = reinterpret_cast<const float4*>(a.table);
+        for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
+            const float4 v = g[i];
+            if (TM == TM_LINEAR)
+                reinterpret_cast<float2*>(smem)[i] = make_float2(v.x, v.y);
+            else
+                reinterpret_cast<float4*>(smem)[i] = v;
+        }
+        __syncthreads();
+    }
+    // entry address = bits(t + 1.5*2^23) * esize + tab_bias (mod 2^32)
+    const unsigned tab_bias = smem_u32(smem) - (unsigned)kMagicBits * esize;
+    const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
+    unsigned long long npairs = 0;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketFwd, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= a.n_items) break;
+        int I = a.items[it];
+        if (I < 0 || I >= a.n_leaves) {
+            if (lane == 0) set_error(a.ctrl, kErrItemIndex);
+            continue;
+        }
+        int4 li = leaf[I];
+        if (li.y <= 0 || li.y > a.max_leaf || li.y > 64 || (long long)li.x + li.y > a.n ||
+            li.z < 0 || li.z >= a.nbox) {
+            if (lane == 0) set_error(a.ctrl, kErrParticleRange);
+            continue;
+        }
+        if (PK) {
+            if (WIDE && prefer_two_per_lane(li.y))
+                fwd_item_pk<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs);
+            else
+                fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
+        } else {
+            if (WIDE && prefer_two_per_lane(li.y))
+                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs);
+            else
+                fwd_item_sc<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
+        }
+    }
+    if (COUNT) {
+        for (int off = 16; off > 0; off >>= 1) npairs += __shfl_xor_sync(kFull, npairs, off);
+        if (lane == 0 && npairs)
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlPairsLo), npairs);
+    }
+    persistent_exit(a.ctrl + kCtrlTicketFwd, a.ctrl + kCtrlDoneFwd);
+}
+
+// Launch and occupancy of the variant PK (explicitly instantiated in
+// p2p_fwd_f32_sc.cu and p2p_fwd_f32_pk.cu).
+template <int TM, int ACC, bool COUNT, bool PK>
+static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
+{
+    auto k = a.max_leaf > 32 ? p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>
+                             : p2p_fwd_f32_kernel<TM, ACC, COUNT, false, PK>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    k<<<a.blocks, a.warps_per_block * 32, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+template <int TM, int ACC, bool PK>
+static int launch_c(const FwdArgs& a, size_t smem, cudaStream_t st)
+{
+    return a.count_pairs ? launch_t<TM, ACC, true, PK>(a, smem, st)
+                         : launch_t<TM, ACC, false, PK>(a, smem, st);
+}
+
+template <bool PK>
+int launch_fwd_f32_variant(const FwdArgs& a, int precision, size_t smem, cudaStream_t st)
+{
+    if (precision == PSR_FP32_EXACT)
+        return a.accum == PSR_ACC_FP64 ? launch_c<TM_EXACT, PSR_ACC_FP64, PK>(a, smem, st)
+                                       : launch_c<TM_EXACT, PSR_ACC_KAHAN32, PK>(a, smem, st);
+    if (a.interp == PSR_LINEAR)
+        return a.accum == PSR_ACC_FP64 ? launch_c<TM_LINEAR, PSR_ACC_FP64, PK>(a, smem, st)
+                                       : launch_c<TM_LINEAR, PSR_ACC_KAHAN32, PK>(a, smem, st);
+    return a.accum == PSR_ACC_FP64 ? launch_c<TM_CUBIC, PSR_ACC_FP64, PK>(a, smem, st)
+                                   : launch_c<TM_CUBIC, PSR_ACC_KAHAN32, PK>(a, smem, st);
+}
+
+template <bool PK>
+const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_leaf)
+{
+#define PSR_PICK(TM, ACC) (max_leaf > 32 ? (const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK> \
+                                         : (const void*)p2p_fwd_f32_kernel<TM, ACC, false, false, PK>)
+    if (precision == PSR_FP32_EXACT)
+        return accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
+    if (interp == PSR_LINEAR)
+        return accum == PSR_ACC_FP64 ? PSR_PICK(TM_LINEAR, PSR_ACC_FP64) : PSR_PICK(TM_LINEAR, PSR_ACC_KAHAN32);
+    return accum == PSR_ACC_FP64 ? PSR_PICK(TM_CUBIC, PSR_ACC_FP64) : PSR_PICK(TM_CUBIC, PSR_ACC_KAHAN32);
+#undef PSR_PICK
+}
+
+}  // namespace psr

@@ -57,6 +57,34 @@ __device__ __forceinline__ void persistent_exit(unsigned* ticket, unsigned* done
     }
 }
 
+// PTX rsqrt.approx.ftz.f32: one SFU instruction, max relative error 2^-22.9.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 32-bit shared-window address of a shared-memory pointer.
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Loads from read-only shared data (the interpolation table): no ordering.
+__device__ __forceinline__ float2 lds_f2(unsigned a)
+{
+    float2 v;
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 lds_f4(unsigned a)
+{
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
 // lanes per stream T (power of two >= n, at least 4), as log2
 __device__ __forceinline__ int stream_log2(int n)
 {

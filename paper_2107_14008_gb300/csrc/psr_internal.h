@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/psr.h"
+#include "psr.h"
 
 namespace psr {
 
@@ -141,6 +141,8 @@ struct FwdArgs {
     int warps_per_block;
     int blocks;
     int max_leaf;
+    int variant;     // FP32 forward: PSR_KERNEL_SCALAR or PSR_KERNEL_PACKED
+    int stage_cap;   // FP32 forward: staged particles per warp
 };
 
 int launch_table(int table_n, int interp, double x_c, void* d_out, void* d_q_out, void* stream);
@@ -149,7 +151,9 @@ int launch_fwd_f64(const FwdArgs& a, void* stream);
 int launch_adj_f32(const FwdArgs& a, int precision, void* stream);
 int launch_adj_f64(const FwdArgs& a, void* stream);
 int fwd_f32_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
-                      int* out);
+                      int cap, int variant, int* out);
+size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap);
+constexpr size_t kSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block
 int fwd_f64_occupancy(int warps, int max_leaf, int* out);
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
                   int* out);

@@ -93,35 +93,52 @@ FP32_VARIANTS = [
 ]
 
 
+KERNELS = [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED]
+
+
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("name,kw", FP32_VARIANTS)
 @pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
-def test_fp32_paths_match_oracle(case, name, kw, accum):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_paths_match_oracle(case, name, kw, accum, kernel):
     b = CASES[case]()
     ref, _, _ = oracle_acc(b, case)
-    acc, _ = gpu_forces(b, psr.Options(accum=accum, **kw), 32)
+    acc, _ = gpu_forces(b, psr.Options(accum=accum, kernel=kernel, **kw), 32)
     assert rel_rms(acc, ref) < 2e-5, name
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("interp", [psr.PSR_LINEAR, psr.PSR_CUBIC])
+def test_wide_leaves_two_targets_per_lane(case, kernel, interp):
+    """max_leaf 64: leaves above 32 particles put two targets on each lane."""
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case)
+    acc, lv = gpu_forces(b, psr.Options(kernel=kernel, interp=interp), 64)
+    assert rel_rms(acc, ref) < 2e-5
 
 
 @pytest.mark.parametrize("case", ["uniform", "clustered"])
 @pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
                                          (psr.PSR_CUBIC, oracle.T_CUBIC)])
 @pytest.mark.parametrize("table_n", [256, 1024])
-def test_table_path_matches_interpolated_oracle(case, interp, mode, table_n):
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+def test_table_path_matches_interpolated_oracle(case, interp, mode, table_n, kernel):
     b = CASES[case]()
     ref, _, _ = oracle_acc(b, case, mode, table_n)
     acc, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP32_TABLE, table_n=table_n,
-                                       interp=interp), 16)
+                                       interp=interp, kernel=kernel), 16)
     assert rel_rms(acc, ref) < 2e-6
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_FP32_TABLE, psr.PSR_FP32_EXACT])
-def test_pair_count_matches_oracle(case, precision):
+@pytest.mark.parametrize("precision,kernel", [(psr.PSR_FP64, 0), (psr.PSR_FP32_TABLE, 1),
+                                              (psr.PSR_FP32_TABLE, 2), (psr.PSR_FP32_EXACT, 1)])
+def test_pair_count_matches_oracle(case, precision, kernel):
     b = CASES[case]()
     _, pairs, _ = oracle_acc(b, case)
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=16).upload()
-    lv.forces(psr.Options(precision=precision, count_pairs=True))
+    lv.forces(psr.Options(precision=precision, count_pairs=True, kernel=kernel))
     got = lv.pair_count()
     # FP32 distances can move a pair within one rounding of r_c across it
     tol = 0 if precision == psr.PSR_FP64 else max(2, int(1e-6 * pairs.sum()))
@@ -238,11 +255,12 @@ def precision_workload():
 
 
 @pytest.mark.parametrize("name,kw", FP32_VARIANTS)
-def test_precision_workload_sampled(precision_workload, name, kw):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_precision_workload_sampled(precision_workload, name, kw, kernel):
     """128^3 NFW (60 % in 4000 halos), L=500: 2000 sampled targets, the full
     launch the benchmark times."""
     b, lv, tg, ref = precision_workload
-    acc = lv.forces(psr.Options(**kw)).double().cpu().numpy()
+    acc = lv.forces(psr.Options(kernel=kernel, **kw)).double().cpu().numpy()
     lv.check()
     assert np.all(np.isfinite(acc))
     assert rel_rms(acc[tg], ref) < 2e-5, name
