@@ -186,6 +186,32 @@ int psr_p2p_adjoint(psr_leaves* h, const psr_opts* opts, const void* d_cot, void
                     void* d_grad_mass, void* cuda_stream);
 
 /*
+ * psr_p2p_forces_noalloc - device: the same accelerations as psr_p2p_forces
+ * (same kernels, same options), for callers that cannot allocate device
+ * memory - code that runs inside a memory pool or arena owned by a host
+ * framework, in a context where an allocation may block, or under a policy
+ * that forbids allocations after start-up.  The paper has no counterpart;
+ * this is an interface addition of this library.
+ *   h      a handle uploaded with psr_upload (its workspace holds the inputs)
+ *   d_acc  device, n x 3, original order, as for psr_p2p_forces
+ * The kernel's scratch (work counters, error word and interpolation table)
+ * is a fixed 66,048-byte __device__ array in the library instead of the
+ * workspace; each device that loads the library holds one copy until the
+ * process exits.  Nothing is allocated by this call or by anything it calls.
+ * Limits and behaviour:
+ *  - PSR_FP32_TABLE accepts table_n <= 4096; larger tables return PSR_E_ARG.
+ *  - The first call on each device looks up the array's device address with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *  - Every call on a device shares the array: each call clears its counters
+ *    and rebuilds the table it needs first, and two calls that overlap on
+ *    the GPU (different streams, no ordering) race on it.
+ *  - Bounds-check errors of these calls land in the shared array and are
+ *    not reported by psr_check; count_pairs results are not readable either.
+ * Errors: as psr_p2p_forces, plus PSR_E_ARG for an oversized table.
+ */
+int psr_p2p_forces_noalloc(psr_leaves* h, const psr_opts* opts, void* d_acc, void* cuda_stream);
+
+/*
  * psr_pair_count - host: number of pairs with 0 < r < r_c counted by the
  * last psr_p2p_forces call made with opts->count_pairs = 1 (waits up to
  * timeout_ms for the stream).  Errors: PSR_E_STATE, PSR_E_TIMEOUT.

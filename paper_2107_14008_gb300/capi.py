@@ -21,7 +21,8 @@ PSR_BUILD_NO_FP64 = 1
 
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
-           "psr_p2p_forces", "psr_p2p_adjoint", "psr_pair_count", "psr_check", "psr_table",
+           "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
+           "psr_check", "psr_table",
            "psr_leaves_host_arrays", "psr_free_leaves", "psr_last_error", "psr_version"]
 
 
@@ -81,6 +82,7 @@ def lib():
     L.psr_leaves_info.argtypes = [vp, ctypes.POINTER(psr_info)]
     L.psr_upload.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.psr_p2p_forces.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp]
+    L.psr_p2p_forces_noalloc.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp]
     L.psr_p2p_adjoint.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, vp, vp]
     L.psr_pair_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
     L.psr_check.argtypes = [vp, vp, ctypes.c_int]
@@ -132,6 +134,13 @@ def psr_upload(h, d_ws, nbytes, stream):
 def psr_p2p_forces(h, opts, d_acc, stream):
     return check(lib().psr_p2p_forces(h, ctypes.byref(opts), ctypes.c_void_p(d_acc),
                                       ctypes.c_void_p(stream)))
+
+
+def psr_p2p_forces_noalloc(h, opts, d_acc, stream):
+    """psr_p2p_forces without any allocation: its scratch is a fixed array in
+    the library (see include/psr.h), for callers that cannot allocate."""
+    return check(lib().psr_p2p_forces_noalloc(h, ctypes.byref(opts), ctypes.c_void_p(d_acc),
+                                              ctypes.c_void_p(stream)))
 
 
 def psr_p2p_adjoint(h, opts, d_cot, d_gpos, d_gmass, stream):

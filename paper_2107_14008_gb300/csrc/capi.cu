@@ -165,6 +165,30 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
 
 }  // namespace
 
+namespace psr {
+
+// Helpers for the allocation-free entry point in noalloc.cu.
+void set_last_error(const std::string& msg) { g_err = msg; }
+
+int prepare_forward(Leaves* h, const psr_opts* opts, FwdArgs* a, int* precision)
+{
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    Opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (o.precision == PSR_FP64 && h->pd.empty())
+        return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
+    const bool fwd32 = o.precision != PSR_FP64;
+    if ((rc = resolve_warps(o, fwd32))) return rc;
+    *a = base_args(h, o);
+    if (fwd32 && (rc = fwd32_smem_config(o, &a->stage_cap))) return rc;
+    if ((rc = grid_blocks(h, o, 0, &a->blocks))) return rc;
+    *precision = o.precision;
+    return PSR_OK;
+}
+
+}  // namespace psr
+
 extern "C" {
 
 const char* psr_last_error(void) { return g_err.c_str(); }
