@@ -176,6 +176,28 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+FWD_SOURCES = ["fwd_f32_common.cuh", "p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu",
+               "kcommon.cuh", "psr_internal.h"]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the forward kernel from the committed ncu
+    summary, if the kernel sources are unchanged since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "p2p_fwd_f32_precision128_dram.md")
+    try:
+        txt = open(path).read()
+        want = txt.split("source_sha256:")[1].split()[0]
+        nbytes = int(txt.split("dram_bytes_per_launch:")[1].split()[0])
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in FWD_SOURCES:
+        with open(os.path.join(ROOT, "paper_2107_14008_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest() == want else None
+
+
 def make_box(args, rank=0):
     import synth
     if args.workload == "adjoint64":
@@ -319,7 +341,8 @@ def run_psr(args):
                          "host_build_s": build_s},
         "pct_fp32_peak_51flop": 100.0 * achieved / peak_tflops,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": measured_traffic() if args.workload == "precision" else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
                                   % (props.multi_processor_count, sm_max, pk_src)},
