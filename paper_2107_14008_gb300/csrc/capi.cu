@@ -84,6 +84,8 @@ int resolve_warps(Opts& o, bool fwd32)
     return PSR_OK;
 }
 
+constexpr int kAdjStageCap = 128;  // adjoint staged particles per warp (2 float4 each)
+
 // Staging capacity per warp; the table and the staging buffers must fit in one
 // block's shared memory.
 int fwd32_smem_config(const Opts& o, int* cap)
@@ -147,7 +149,8 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
     if (bps == 0) {
         int occ = 0, e;
         if (adjoint)
-            e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n, &occ);
+            e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
+                              kAdjStageCap, &occ);
         else if (o.precision == PSR_FP64)
             e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
         else {
@@ -323,13 +326,16 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     if (rc) return rc;
     if (o.precision == PSR_FP64 && h->pd.empty())
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
-    if (o.precision == PSR_FP32_TABLE && o.interp == PSR_CUBIC && o.table_n > 4096)
-        return fail(PSR_E_ARG, "cubic adjoint tables hold at most 4096 intervals (shared memory)");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = resolve_warps(o, false))) return rc;
     if ((rc = ensure_table(h, o, st))) return rc;
     FwdArgs a = base_args(h, o);
     a.cot = d_cot;
+    a.stage_cap = kAdjStageCap;
+    if (o.precision != PSR_FP64 &&
+        adj_f32_smem(o.precision, o.interp, o.table_n, o.warps, kAdjStageCap) > kSmemPerBlock)
+        return fail(PSR_E_ARG, "adjoint table and staging buffers exceed shared memory; "
+                               "use fewer warps or a smaller table");
     a.out = d_grad_pos;
     a.out_m = d_grad_mass;
     if ((rc = grid_blocks(h, o, 1, &a.blocks))) return rc;

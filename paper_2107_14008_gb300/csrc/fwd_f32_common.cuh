@@ -73,10 +73,11 @@ constexpr int kMetaPerWarp = 32; // entries per chunk (one per lane)
 // Stages one chunk starting at entry e0; returns the number of entries taken
 // and sets nst to the number of staged particles.  Staged coordinates are
 // multiplied by sc (the kernels' working unit per FP32 coordinate unit).
-// PK = false: one float4 (x, y, z, m) per particle; PK = true: particle pairs
+// MODE 0: one float4 (x, y, z, m) per particle; MODE 1: particle pairs
 // interleaved for packed arithmetic, an odd count padded with a massless
-// particle far beyond the cutoff.
-template <bool PK>
+// particle far beyond the cutoff; MODE 2 (adjoint): two float4 per particle,
+// (x, y, z, m) and the cotangent (c_x, c_y, c_z, 0) from a.cot_sorted.
+template <int MODE>
 __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long long re,
                                            int4 ci, float unit, float sc, int cap,
                                            float4* __restrict__ stage,
@@ -132,7 +133,7 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
     // slot p belongs to the entry k with excl_k <= p < excl_{k+1}: count the
     // entry starts at or before p with a position bitmask per 32-slot round
     int C = 0;
-    for (int p0 = 0; p0 < nst + (PK ? (nst & 1) : 0); p0 += 32) {
+    for (int p0 = 0; p0 < nst + (MODE == 1 ? (nst & 1) : 0); p0 += 32) {
         const int rel = excl - p0;
         const unsigned bit = (lane < ntake && rel >= 0 && rel < 32) ? (1u << rel) : 0u;
         const unsigned M = __reduce_or_sync(kFull, bit);
@@ -142,17 +143,22 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
         if (p < nst) {
             const float4 m = meta[k];
             const float4 v = __ldg(pf + (__float_as_int(m.x) + p));
-            if (PK) {
+            if (MODE == 1) {
                 // pair j = p/2 occupies two float4: (x0, x1, y0, y1), (z0, z1, m0, m1)
                 float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + (p & 1);
                 d[0] = fmaf(v.x, sc, m.y);
                 d[2] = fmaf(v.y, sc, m.z);
                 d[4] = fmaf(v.z, sc, m.w);
                 d[6] = v.w;
-            } else {
+            } else if (MODE == 0) {
                 stage[p] = make_float4(fmaf(v.x, sc, m.y), fmaf(v.y, sc, m.z), fmaf(v.z, sc, m.w), v.w);
+            } else {
+                const float4 c = __ldg(reinterpret_cast<const float4*>(a.cot_sorted) +
+                                       (__float_as_int(m.x) + p));
+                stage[2 * p] = make_float4(fmaf(v.x, sc, m.y), fmaf(v.y, sc, m.z), fmaf(v.z, sc, m.w), v.w);
+                stage[2 * p + 1] = c;
             }
-        } else if (PK && p == nst && (nst & 1)) {
+        } else if (MODE == 1 && p == nst && (nst & 1)) {
             // pad an odd chunk with a massless particle far beyond the cutoff
             float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + 1;
             d[0] = d[2] = d[4] = 1e18f;
@@ -308,7 +314,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
     const float2 mhalf = make_float2(-0.5f, -0.5f);
     while (e0 < re) {
         int nst;
-        e0 += stage_chunk<true>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        e0 += stage_chunk<1>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
         if (on) {
             const int npair = (nst + 1) >> 1;
 #pragma unroll 1
@@ -413,7 +419,7 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
     const float eps2 = kEps2 * sc * sc;
     while (e0 < re) {
         int nst;
-        e0 += stage_chunk<false>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        e0 += stage_chunk<0>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
         if (on) {
 #pragma unroll 2
             for (int k = s; k < nst; k += S) {

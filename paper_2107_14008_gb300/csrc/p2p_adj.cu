@@ -12,35 +12,36 @@
 // gathered into Morton order.  Same work decomposition as the forward.
 #include <cuda_runtime.h>
 
-#include "kcommon.cuh"
+#include "fwd_f32_common.cuh"
 
 namespace psr {
 
-enum { TA_EXACT = 0, TA_LINEAR = 1, TA_CUBIC = 2 };
 constexpr float kFourOverSqrtPi = 2.2567583341910251f;
 
+// T and Q = exp(-x^2) at table coordinate t = u - 1/2 (u = x N / x_c).
+// Linear table: one float4 (T mid, T diff, Q mid, Q diff) per interval;
+// cubic: the T and Q coefficient float4s in two arrays.  Entry N is zero.
 template <int TM>
-__device__ __forceinline__ void eval_TQ(float x, const float* tT, const float* tQ, float inv_h,
-                                        float nmax, float x_c, float& T, float& Q)
+__device__ __forceinline__ void eval_TQ(float t, float x, float x_c, unsigned tab_bias,
+                                        unsigned q_off, float nmax, float& T, float& Q)
 {
-    if (TM == TA_EXACT) {
-        float q = expf(-x * x);
-        float t = erfcf(x) + kTwoOverSqrtPi * x * q;
-        bool in = x < x_c;
-        T = in ? t : 0.0f;
+    if (TM == TM_EXACT) {
+        const float q = expf(-x * x);
+        const float tv = erfcf(x) + kTwoOverSqrtPi * x * q;
+        const bool in = x < x_c;
+        T = in ? tv : 0.0f;
         Q = in ? q : 0.0f;
     } else {
-        float t = fminf(fmaf(x, inv_h, -0.5f), nmax);
-        float fk = t + kMagic;
-        int k = __float_as_int(fk) - kMagicBits;
-        float f = t - (fk - kMagic);
-        if (TM == TA_LINEAR) {
-            float4 c = reinterpret_cast<const float4*>(tT)[k];  // (T mid, T diff, Q mid, Q diff)
+        t = fminf(t, nmax);
+        const float fk = t + kMagic;
+        const float f = t - (fk - kMagic);
+        const unsigned a = (unsigned)__float_as_int(fk) * 16u + tab_bias;
+        const float4 c = lds_f4(a);
+        if (TM == TM_LINEAR) {
             T = fmaf(f, c.y, c.x);
             Q = fmaf(f, c.w, c.z);
         } else {
-            float4 c = reinterpret_cast<const float4*>(tT)[k];
-            float4 d = reinterpret_cast<const float4*>(tQ)[k];
+            const float4 d = lds_f4(a + q_off);
             T = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
             Q = fmaf(f, fmaf(f, fmaf(f, d.w, d.z), d.y), d.x);
         }
@@ -66,177 +67,179 @@ struct Acc4 {
             f[i] = 0.0f;
         }
     }
-    __device__ __forceinline__ void reduce(int lgT)
-    {
-        for (int off = 1 << lgT; off < 32; off <<= 1) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (ACC == PSR_ACC_FP64) {
-                    d[i] += __shfl_xor_sync(kFull, d[i], off);
-                } else {
-                    float os = __shfl_xor_sync(kFull, s[i], off), oc = __shfl_xor_sync(kFull, c[i], off);
-                    float ss, ee;
-                    two_sum(s[i], os, ss, ee);
-                    s[i] = ss;
-                    c[i] += oc + ee;
-                }
-            }
-        }
-    }
-    __device__ __forceinline__ float get(int i, float g) const
-    {
-        return ACC == PSR_ACC_FP64 ? (float)(d[i] * (double)g) : (s[i] + c[i]) * g;
-    }
 };
 
+// One target leaf on one warp (same decomposition as the forward kernels;
+// staged payload: two float4 per source particle).
 template <int TM, int ACC, int R>
-__device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, const float* tT,
-                                         const float* tQ)
+__device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
+                                         unsigned q_off, float4* __restrict__ stage,
+                                         float4* __restrict__ meta)
 {
     const int lane = threadIdx.x & 31;
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
     const float4* __restrict__ cs = reinterpret_cast<const float4*>(a.cot_sorted);
-    const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
     const int nI = li.y;
-    const int lgT = (R == 2) ? 5 : stream_log2(nI);
-    const int q = lane & ((1 << lgT) - 1);
-    const int s = lane >> lgT;
-    const int S = 32 >> lgT;
+    const int T = (nI + R - 1) / R;
+    const int S = 32 / T;
+    const int s = lane / T;
+    const int q = lane - s * T;
+    const bool on = s < S;
     const BoxDev& bx = a.boxes[li.z];
-    const float unit = bx.unit, x_c = bx.x_c;
-    const float nmax = (float)a.table_n, inv_h = (float)a.table_n / x_c;
+    const float x_c = bx.x_c;
+    const float nmax = (float)a.table_n;
+    // working unit: table intervals for the table path, x for the exact path
+    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    const float xscale = 1.0f / sc;
+    const float c4 = kFourOverSqrtPi / (sc * sc * sc);  // (4/sqrt(pi)) in working units
+    const float unit = bx.unit;
     const int4 ci = lcen[I];
 
     float4 xi[R], ck[R];
     bool act[R];
-    float t3[R][3], f[R][4];
+    float f[R][4];
     Acc4<ACC> acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        int t = q + 32 * r;
-        act[r] = t < nI;
+        const int t = q + T * r;
+        act[r] = on && t < nI;
         xi[r] = pf[li.x + (act[r] ? t : 0)];
+        xi[r].x *= sc;
+        xi[r].y *= sc;
+        xi[r].z *= sc;
         ck[r] = cs[li.x + (act[r] ? t : 0)];
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[r][i] = 0.0f;
-        t3[r][0] = t3[r][1] = t3[r][2] = 0.0f;
     }
-    int since = 0;
     const long long re = a.rowptr[I + 1];
-    long long e = a.rowptr[I] + s;
-    int j = 0, jend = 0;
-    for (;;) {
-        if (j >= jend) {
-            bool found = false;
-            while (e < re) {
-                unsigned ent = a.pairs[e];
-                e += S;
-                int J = (int)(ent >> 5);
-                unsigned code = ent & 31u;
-                if (J >= a.n_leaves || code >= (unsigned)kShiftCodes) {
-                    set_error(a.ctrl, J >= a.n_leaves ? kErrLeafIndex : kErrShiftCode);
-                    continue;
-                }
-                int4 lj = leaf[J];
-                if (lj.x < 0 || lj.y < 0 || (long long)lj.x + lj.y > a.n) {
-                    set_error(a.ctrl, kErrParticleRange);
-                    continue;
-                }
-                int4 cj = lcen[J];
-                int nx, ny, nz;
-                decode_shift(code, nx, ny, nz);
-                float ox = (float)(cj.x - ci.x + nx * (1 << kCentreShift)) * unit;
-                float oy = (float)(cj.y - ci.y + ny * (1 << kCentreShift)) * unit;
-                float oz = (float)(cj.z - ci.z + nz * (1 << kCentreShift)) * unit;
-                if (since >= a.fold_every) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r].fold(f[r]);
-                    since = 0;
-                }
+    long long e0 = a.rowptr[I];
+    while (e0 < re) {
+        int nst;
+        e0 += stage_chunk<2>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (on) {
+#pragma unroll 1
+            for (int k = s; k < nst; k += S) {
+                const float4 p = stage[2 * k];
+                const float4 c = stage[2 * k + 1];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    t3[r][0] = xi[r].x - ox;
-                    t3[r][1] = xi[r].y - oy;
-                    t3[r][2] = xi[r].z - oz;
+                    const float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float rinv = rsqrt_ftz(r2);
+                    float Tv, Qv;
+                    eval_TQ<TM>(fmaf(r2, rinv, -0.5f), r2 * rinv * xscale, x_c, tab_bias, q_off,
+                                nmax, Tv, Qv);
+                    const float rinv2 = rinv * rinv;
+                    float tr3 = Tv * rinv2 * rinv;                                // T/u^3
+                    float hh = -rinv2 * fmaf(3.0f, tr3, c4 * Qv);                 // g'(r)/r
+                    // the self pair and coincident pairs contribute nothing
+                    const bool nz = r2 > 0.0f;
+                    tr3 = nz ? tr3 : 0.0f;
+                    hh = nz ? hh : 0.0f;
+                    const float vx = fmaf(xi[r].w, c.x, -p.w * ck[r].x);
+                    const float vy = fmaf(xi[r].w, c.y, -p.w * ck[r].y);
+                    const float vz = fmaf(xi[r].w, c.z, -p.w * ck[r].z);
+                    const float hd = hh * fmaf(dx, vx, fmaf(dy, vy, dz * vz));
+                    f[r][0] = fmaf(tr3, vx, fmaf(hd, dx, f[r][0]));
+                    f[r][1] = fmaf(tr3, vy, fmaf(hd, dy, f[r][1]));
+                    f[r][2] = fmaf(tr3, vz, fmaf(hd, dz, f[r][2]));
+                    f[r][3] = fmaf(tr3, fmaf(dx, c.x, fmaf(dy, c.y, dz * c.z)), f[r][3]);
                 }
-                since += lj.y;
-                j = lj.x;
-                jend = lj.x + lj.y;
-                found = true;
-                break;
             }
-            if (!found) break;
-        }
-        const float4 p = __ldg(pf + j);
-        const float4 c = __ldg(cs + j);
-        ++j;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float dx = p.x - t3[r][0], dy = p.y - t3[r][1], dz = p.z - t3[r][2];
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float rinv = rsqrtf(r2);
-            float x = r2 * rinv;
-            float T, Q;
-            eval_TQ<TM>(x, tT, tQ, inv_h, nmax, x_c, T, Q);
-            float rinv2 = rinv * rinv;
-            float tr3 = T * rinv2 * rinv;                        // T / x^3
-            float hh = -rinv2 * fmaf(3.0f, tr3, kFourOverSqrtPi * Q);  // -3T/x^5 - (4/sqrt(pi)) Q/x^2
-            bool nz = r2 > 0.0f;
-            tr3 = nz ? tr3 : 0.0f;
-            hh = nz ? hh : 0.0f;
-            float vx = fmaf(xi[r].w, c.x, -p.w * ck[r].x);
-            float vy = fmaf(xi[r].w, c.y, -p.w * ck[r].y);
-            float vz = fmaf(xi[r].w, c.z, -p.w * ck[r].z);
-            float hd = hh * fmaf(dx, vx, fmaf(dy, vy, dz * vz));
-            f[r][0] = fmaf(tr3, vx, fmaf(hd, dx, f[r][0]));
-            f[r][1] = fmaf(tr3, vy, fmaf(hd, dy, f[r][1]));
-            f[r][2] = fmaf(tr3, vz, fmaf(hd, dz, f[r][2]));
-            f[r][3] = fmaf(tr3, fmaf(dx, c.x, fmaf(dy, c.y, dz * c.z)), f[r][3]);
+            for (int r = 0; r < R; ++r) acc[r].fold(f[r]);
         }
+        __syncwarp();
     }
+    // dL/dx = G/(8 r_s^3) sc^3 sum,  dL/dm = -G/(4 r_s^2) sc^2 sum
+    const float gx = bx.g_adj * sc * sc * sc;
+    const float gm = -bx.g_adjm * sc * sc;
+    // combine the S stream partials through the staging buffer
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        acc[r].fold(f[r]);
-        acc[r].reduce(lgT);
-    }
-    if (s == 0) {
+        if (ACC == PSR_ACC_FP64) {
+            double* red = reinterpret_cast<double*>(stage);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (!act[r]) continue;
-            int idx = a.perm[li.x + q + 32 * r];
-            float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
-            o[0] = acc[r].get(0, bx.g_adj);
-            o[1] = acc[r].get(1, bx.g_adj);
-            o[2] = acc[r].get(2, bx.g_adj);
-            if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = acc[r].get(3, -bx.g_adjm);
+            for (int i = 0; i < 4; ++i) red[4 * lane + i] = acc[r].d[i];
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                double t4[4] = {acc[r].d[0], acc[r].d[1], acc[r].d[2], acc[r].d[3]};
+                for (int t = 1; t < S; ++t)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t4[i] += red[4 * (lane + t * T) + i];
+                const int idx = a.perm[li.x + q + T * r];
+                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                o[0] = (float)(t4[0] * (double)gx);
+                o[1] = (float)(t4[1] * (double)gx);
+                o[2] = (float)(t4[2] * (double)gx);
+                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (float)(t4[3] * (double)gm);
+            }
+        } else {
+            float* red = reinterpret_cast<float*>(stage);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                red[8 * lane + 2 * i] = acc[r].s[i];
+                red[8 * lane + 2 * i + 1] = acc[r].c[i];
+            }
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                float hi[4], lo[4], u, v;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    hi[i] = acc[r].s[i];
+                    lo[i] = acc[r].c[i];
+                }
+                for (int t = 1; t < S; ++t)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float* o = red + 8 * (lane + t * T) + 2 * i;
+                        two_sum(hi[i], o[0], u, v);
+                        hi[i] = u;
+                        lo[i] += o[1] + v;
+                    }
+                const int idx = a.perm[li.x + q + T * r];
+                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                o[0] = (hi[0] + lo[0]) * gx;
+                o[1] = (hi[1] + lo[1]) * gx;
+                o[2] = (hi[2] + lo[2]) * gx;
+                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (hi[3] + lo[3]) * gm;
+            }
         }
+        __syncwarp();
     }
 }
 
+// Shared memory: the table (T and Q), then per warp a staging buffer of
+// stage_cap particles x 2 float4 plus 32 entry records.
 template <int TM, int ACC, bool WIDE>
-__global__ void __launch_bounds__(256) p2p_adj_f32_kernel(const FwdArgs a)
+__global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    float* tT = reinterpret_cast<float*>(smem);
-    float* tQ = tT + 4 * (a.table_n + 1);
-    if (TM != TA_EXACT) {
+    const int warp = threadIdx.x >> 5;
+    const size_t tab_bytes = TM == TM_EXACT ? 0
+                           : (size_t)(a.table_n + 1) * (TM == TM_LINEAR ? 16 : 32);
+    float4* stage = reinterpret_cast<float4*>(smem + tab_bytes) +
+                    (size_t)warp * (2 * a.stage_cap + kMetaPerWarp);
+    float4* meta = stage + 2 * a.stage_cap;
+    if (TM != TM_EXACT) {
         const float4* g = reinterpret_cast<const float4*>(a.table);
         const float4* gq = g + (kMaxTableN + 1);
-        float4* sT = reinterpret_cast<float4*>(tT);
-        float4* sQ = reinterpret_cast<float4*>(tQ);
+        float4* sT = reinterpret_cast<float4*>(smem);
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
-            if (TM == TA_LINEAR) {
-                float4 u = g[i], v = gq[i];
+            if (TM == TM_LINEAR) {
+                const float4 u = g[i], v = gq[i];
                 sT[i] = make_float4(u.x, u.y, v.x, v.y);
             } else {
                 sT[i] = g[i];
-                sQ[i] = gq[i];
+                sT[a.table_n + 1 + i] = gq[i];
             }
         }
         __syncthreads();
     }
+    const unsigned tab_bias = smem_u32(smem) - (unsigned)kMagicBits * 16u;
+    const unsigned q_off = (unsigned)(a.table_n + 1) * 16u;
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     for (;;) {
         int it = 0;
@@ -249,15 +252,15 @@ __global__ void __launch_bounds__(256) p2p_adj_f32_kernel(const FwdArgs a)
             continue;
         }
         int4 li = leaf[I];
-        if (li.y <= 0 || li.y > a.max_leaf || (long long)li.x + li.y > a.n || li.z < 0 ||
-            li.z >= a.nbox) {
+        if (li.y <= 0 || li.y > a.max_leaf || li.y > 64 || (long long)li.x + li.y > a.n ||
+            li.z < 0 || li.z >= a.nbox) {
             if (lane == 0) set_error(a.ctrl, kErrParticleRange);
             continue;
         }
-        if (WIDE && li.y > 32)
-            adj_item<TM, ACC, 2>(a, I, li, tT, tQ);
+        if (WIDE && prefer_two_per_lane(li.y))
+            adj_item<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta);
         else
-            adj_item<TM, ACC, 1>(a, I, li, tT, tQ);
+            adj_item<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
     }
     persistent_exit(a.ctrl + kCtrlTicketAdj, a.ctrl + kCtrlDoneAdj);
 }
@@ -415,17 +418,17 @@ __global__ void gather_cot_kernel(const T* __restrict__ cot, const int32_t* __re
     cs[k] = v;
 }
 
-static size_t adj_smem(int precision, int interp, int table_n)
+size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 {
-    if (precision != PSR_FP32_TABLE) return 0;
-    return (size_t)(table_n + 1) * (interp == PSR_LINEAR ? 16 : 32);
+    size_t tab = precision != PSR_FP32_TABLE ? 0
+               : (size_t)(table_n + 1) * (interp == PSR_LINEAR ? 16 : 32);
+    return tab + (size_t)warps * (2 * cap + kMetaPerWarp) * 16;
 }
 
 template <int TM, int ACC>
 static int launch_adj_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    bool wide = a.max_leaf > 32;
-    auto k = wide ? p2p_adj_f32_kernel<TM, ACC, true> : p2p_adj_f32_kernel<TM, ACC, false>;
+    auto k = a.max_leaf > 32 ? p2p_adj_f32_kernel<TM, ACC, true> : p2p_adj_f32_kernel<TM, ACC, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -442,15 +445,15 @@ int launch_adj_f32(const FwdArgs& a, int precision, void* stream)
         reinterpret_cast<const float*>(a.cot), a.perm, reinterpret_cast<float4*>(a.cot_sorted), a.n);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return (int)e0;
-    size_t smem = adj_smem(precision, a.interp, a.table_n);
+    size_t smem = adj_f32_smem(precision, a.interp, a.table_n, a.warps_per_block, a.stage_cap);
     if (precision == PSR_FP32_EXACT)
-        return a.accum == PSR_ACC_FP64 ? launch_adj_t<TA_EXACT, PSR_ACC_FP64>(a, smem, st)
-                                       : launch_adj_t<TA_EXACT, PSR_ACC_KAHAN32>(a, smem, st);
+        return a.accum == PSR_ACC_FP64 ? launch_adj_t<TM_EXACT, PSR_ACC_FP64>(a, smem, st)
+                                       : launch_adj_t<TM_EXACT, PSR_ACC_KAHAN32>(a, smem, st);
     if (a.interp == PSR_LINEAR)
-        return a.accum == PSR_ACC_FP64 ? launch_adj_t<TA_LINEAR, PSR_ACC_FP64>(a, smem, st)
-                                       : launch_adj_t<TA_LINEAR, PSR_ACC_KAHAN32>(a, smem, st);
-    return a.accum == PSR_ACC_FP64 ? launch_adj_t<TA_CUBIC, PSR_ACC_FP64>(a, smem, st)
-                                   : launch_adj_t<TA_CUBIC, PSR_ACC_KAHAN32>(a, smem, st);
+        return a.accum == PSR_ACC_FP64 ? launch_adj_t<TM_LINEAR, PSR_ACC_FP64>(a, smem, st)
+                                       : launch_adj_t<TM_LINEAR, PSR_ACC_KAHAN32>(a, smem, st);
+    return a.accum == PSR_ACC_FP64 ? launch_adj_t<TM_CUBIC, PSR_ACC_FP64>(a, smem, st)
+                                   : launch_adj_t<TM_CUBIC, PSR_ACC_KAHAN32>(a, smem, st);
 }
 
 int launch_adj_f64(const FwdArgs& a, void* stream)
@@ -466,22 +469,24 @@ int launch_adj_f64(const FwdArgs& a, void* stream)
     return (int)cudaGetLastError();
 }
 
-int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n, int* out)
+int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
+                  int cap, int* out)
 {
-    bool wide = max_leaf > 32;
-    size_t smem = adj_smem(precision, interp, table_n);
+    const bool wide = max_leaf > 32;
+    size_t smem = 0;
     const void* f;
     if (precision == PSR_FP64) {
         f = wide ? (const void*)p2p_adj_f64_kernel<true> : (const void*)p2p_adj_f64_kernel<false>;
     } else {
+        smem = adj_f32_smem(precision, interp, table_n, warps, cap);
 #define PSR_PICK(TM, ACC) (wide ? (const void*)p2p_adj_f32_kernel<TM, ACC, true> \
                                 : (const void*)p2p_adj_f32_kernel<TM, ACC, false>)
         if (precision == PSR_FP32_EXACT)
-            f = accum == PSR_ACC_FP64 ? PSR_PICK(TA_EXACT, PSR_ACC_FP64) : PSR_PICK(TA_EXACT, PSR_ACC_KAHAN32);
+            f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
         else if (interp == PSR_LINEAR)
-            f = accum == PSR_ACC_FP64 ? PSR_PICK(TA_LINEAR, PSR_ACC_FP64) : PSR_PICK(TA_LINEAR, PSR_ACC_KAHAN32);
+            f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_LINEAR, PSR_ACC_FP64) : PSR_PICK(TM_LINEAR, PSR_ACC_KAHAN32);
         else
-            f = accum == PSR_ACC_FP64 ? PSR_PICK(TA_CUBIC, PSR_ACC_FP64) : PSR_PICK(TA_CUBIC, PSR_ACC_KAHAN32);
+            f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_CUBIC, PSR_ACC_FP64) : PSR_PICK(TM_CUBIC, PSR_ACC_KAHAN32);
 #undef PSR_PICK
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -156,6 +156,7 @@ size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap);
 constexpr size_t kSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block
 int fwd_f64_occupancy(int warps, int max_leaf, int* out);
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
-                  int* out);
+                  int cap, int* out);
+size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap);
 
 }  // namespace psr
