@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--accum", default="fp64", choices=["fp64", "kahan"])
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--adjoint-steps", type=int, default=3)
+    p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--no-variants", dest="variants", action="store_false",
+                   help="skip the precision study (one launch per T variant)")
     p.add_argument("--cpu-targets", type=int, default=100000,
                    help="targets in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -124,7 +128,60 @@ class Clocks:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def cpu_baseline(b, acc_gpu, n_targets, seed=2024):
+PRECISION_VARIANTS = [
+    ("table linear 1024", dict(table_n=1024, interp=0)),
+    ("table linear 4096", dict(table_n=4096, interp=0)),
+    ("table cubic 1024", dict(table_n=1024, interp=1)),
+    ("table cubic 4096", dict(table_n=4096, interp=1)),
+    ("exact erfcf/expf", dict(precision=1)),
+]
+
+
+def run_batch(args, psr, torch, dev, stream, flush):
+    """64 boxes, N log-uniform in [8^3, 64^3], L in [50, 400], half uniform and
+    half NFW-clustered, in one handle and one launch per step."""
+    import synth
+    boxes = synth.batch()
+    t0 = time.perf_counter()
+    lv = psr.Leaves.build_batch([(x.pos, x.mass, x.L, x.r_s, x.r_c, x.G) for x in boxes],
+                                max_leaf=32, fp64=False)
+    build_s = time.perf_counter() - t0
+    lv.upload(dev)
+    best, _ = lv.autotune(psr.Options(), reps=2)
+    out = torch.empty((lv.n, 3), dtype=torch.float32, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        lv.forces(best, out=out)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        lv.forces(best, out=out)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    evs = []
+    for k in range(args.batch_steps):
+        flush.fill_(k & 255)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        graph.replay()
+        s1.record(stream)
+        evs.append((s0, s1))
+    torch.cuda.synchronize()
+    lv.check()
+    ms = sum(a.elapsed_time(e) for a, e in evs) / args.batch_steps
+    ev = lv.evaluated_pairs
+    return {"value": ev / (ms / 1e3) / 1e9, "unit": "G pair-interactions/s", "ms_per_step": ms,
+            "boxes": len(boxes), "n": int(lv.n), "evaluated_per_step": int(ev),
+            "host_build_s": build_s, "launch": "one persistent launch per step, CUDA graph replay",
+            "tile_shape": {"kernel": "packed pairs" if best.kernel == 2 else "scalar streams",
+                           "warps_per_block": best.warps_per_block,
+                           "source_tile": best.source_tile},
+            "path": "FP32, linear 1024 table, FP64 fold"}
+
+
+def cpu_baseline(b, acc_gpu, n_targets, seed=2024, return_ref=False):
     """FP64 oracle on a bounded sample of targets (all sources), host cores."""
     import numpy as np
     import oracle
@@ -139,11 +196,14 @@ def cpu_baseline(b, acc_gpu, n_targets, seed=2024):
     if acc_gpu is not None:
         d = acc_gpu[tg] - ref
         err = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
-    return {"value": float(pairs.sum()) / dt / 1e9, "unit": "G pair-interactions/s",
-            "cores": threads, "kind": "oracle",
-            "sample": "%d random targets of the workload against all %d sources (within-cutoff "
-                      "pairs counted), cell-list FP64 brute force, %.1f s" % (tg.size, b.n, dt),
-            "seconds": dt, "pairs": int(pairs.sum())}, err, tg.size
+    res = {"value": float(pairs.sum()) / dt / 1e9, "unit": "G pair-interactions/s",
+           "cores": threads, "kind": "oracle",
+           "sample": "%d random targets of the workload against all %d sources (within-cutoff "
+                     "pairs counted), cell-list FP64 brute force, %.1f s" % (tg.size, b.n, dt),
+           "seconds": dt, "pairs": int(pairs.sum())}
+    if return_ref:
+        return res, err, tg, ref
+    return res, err, tg.size
 
 
 def run_reference(args):
@@ -299,6 +359,60 @@ def run_psr(args):
                 "ms_per_step": ms64,
                 "fp32_table_rel_rms_vs_fp64_path": float(np.sqrt(np.sum(d * d) / np.sum(ref64 ** 2)))}
 
+    # adjoint (FP32 table) on the same leaf set, same timing rules
+    adj = None
+    if args.adjoint_steps > 0:
+        cot = torch.tensor(np.random.default_rng(5).standard_normal((b.n, 3)), dtype=torch.float32,
+                           device=dev)
+        gp = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+        gm = torch.empty((b.n,), dtype=torch.float32, device=dev)
+        lv.adjoint(cot, opts, gp, gm)
+        torch.cuda.synchronize()
+        ea = []
+        for k in range(args.adjoint_steps):
+            flush.fill_(k & 255)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            lv.adjoint(cot, opts, gp, gm)
+            s1.record(stream)
+            ea.append((s0, s1))
+        torch.cuda.synchronize()
+        ms_a = sum(a.elapsed_time(e) for a, e in ea) / args.adjoint_steps
+        adj = {"value": evaluated / (ms_a / 1e3) / 1e9, "unit": "G pair-interactions/s",
+               "ms_per_step": ms_a, "path": "FP32 adjoint (dL/dx, dL/dm), same table and pairs"}
+        if args.fp64_steps > 0:
+            g64, m64 = lv.adjoint(cot.double(), psr.Options(precision=psr.PSR_FP64))
+            dg = gp.double() - g64
+            dm = gm.double() - m64
+            adj["rel_rms_vs_fp64_path"] = {
+                "dL_dx": float(torch.sqrt((dg * dg).sum() / (g64 * g64).sum())),
+                "dL_dm": float(torch.sqrt((dm * dm).sum() / (m64 * m64).sum()))}
+        lv.check()
+
+    # the precision study: every T variant and accumulation, one launch each
+    variants = []
+    if args.variants:
+        for name, kw in PRECISION_VARIANTS:
+            for accn, accv in (("fp64", psr.PSR_ACC_FP64), ("kahan", psr.PSR_ACC_KAHAN32)):
+                o = psr.Options(accum=accv, **kw)
+                out = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+                lv.forces(o, out=out)
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                lv.forces(o, out=out)
+                s1.record(stream)
+                torch.cuda.synchronize()
+                variants.append({"variant": name, "accum": accn,
+                                 "value": evaluated / (s0.elapsed_time(s1) / 1e3) / 1e9,
+                                 "acc": out.double().cpu().numpy()})
+        lv.check()
+
+    # batched workload: 64 boxes in one persistent launch, autotuned tile shape,
+    # replayed from a CUDA graph
+    batch = None
+    if args.batch_steps > 0:
+        batch = run_batch(args, psr, torch, dev, stream, flush)
+
     # end to end through the public API, host buffers, copies inside the region
     e2e = None
     if args.e2e_steps > 0:
@@ -322,7 +436,16 @@ def run_psr(args):
 
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
-        cb, err, _ = cpu_baseline(b, acc32, args.cpu_targets)
+        cb, err, tg, ref = cpu_baseline(b, acc32, args.cpu_targets, return_ref=True)
+        for v in variants:
+            d = v["acc"][tg] - ref
+            rel = np.linalg.norm(d, axis=1) / np.maximum(np.linalg.norm(ref, axis=1),
+                                                         1e-3 * np.sqrt(np.mean(np.sum(ref * ref, 1))))
+            v["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+            v["max_rel_err"] = float(rel.max())
+            v["p99_rel_err"] = float(np.percentile(rel, 99))
+    for v in variants:
+        v.pop("acc", None)
     pk, pk_src = peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -347,12 +470,16 @@ def run_psr(args):
                      "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
                                   % (props.multi_processor_count, sm_max, pk_src)},
         "fp64_path": fp64,
+        "adjoint": adj,
+        "batch": batch,
+        "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
                         "sampled_targets": None if cb is None else args.cpu_targets},
         "e2e": e2e,
         "cpu_baseline": None if cb is None else {k: cb[k] for k in
                                                   ("value", "unit", "cores", "kind", "sample")},
         "gpu_launches": args.steps,
+        "tile_shape": {"kernel": "scalar streams", "warps_per_block": 8, "source_tile": 256},
         "clocks": clocks,
         "device": props.name,
     }

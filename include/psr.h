@@ -91,7 +91,10 @@ typedef struct {
                             0 = default (64)                                  */
     int count_pairs;     /* 1: also count pairs with 0 < r < r_c (slower)     */
     int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED (FP32 forward) */
-    int reserved[7];     /* must be zero                                      */
+    int source_tile;     /* FP32 kernels: source particles staged per warp in
+                            shared memory, 64 | 128 | 256 and >= the largest
+                            leaf; 0 = default (forward 256, adjoint 128)    */
+    int reserved[6];     /* must be zero                                      */
 } psr_opts;
 
 typedef struct {
@@ -210,6 +213,25 @@ int psr_p2p_adjoint(psr_leaves* h, const psr_opts* opts, const void* d_cot, void
  * Errors: as psr_p2p_forces, plus PSR_E_ARG for an oversized table.
  */
 int psr_p2p_forces_noalloc(psr_leaves* h, const psr_opts* opts, void* d_acc, void* cuda_stream);
+
+/*
+ * psr_autotune - host + device: pick the tile shape of the FP32 forward
+ * kernel for this leaf set.  Starting from *base (precision, table, interp
+ * and accumulation are kept), times every candidate of
+ *   kernel      PSR_KERNEL_SCALAR | PSR_KERNEL_PACKED  (sources per lane
+ *               and iteration: 1 | 2)
+ *   warps       4 | 8 per block
+ *   source_tile 64 | 128 | 256 staged source particles per warp
+ * that fits shared memory and the largest leaf, with CUDA events on
+ * `cuda_stream` (one warm-up and `reps` timed launches each, best time
+ * kept), writing the accelerations to d_acc (n x 3 FP32, overwritten).
+ * The best options go to *best and their time in milliseconds to *best_ms
+ * (may be NULL).  Synchronises the stream; every wait is bounded by
+ * timeout_ms (PSR_E_TIMEOUT).  Errors: PSR_E_ARG (FP64 precision, reps < 1),
+ * PSR_E_STATE (not uploaded), PSR_E_CUDA, PSR_E_TIMEOUT.
+ */
+int psr_autotune(psr_leaves* h, const psr_opts* base, void* d_acc, void* cuda_stream, int reps,
+                 int timeout_ms, psr_opts* best, float* best_ms);
 
 /*
  * psr_pair_count - host: number of pairs with 0 < r < r_c counted by the

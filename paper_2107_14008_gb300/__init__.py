@@ -33,6 +33,7 @@ class Options:
     fold_every: int = 0
     count_pairs: bool = False
     kernel: int = 0
+    source_tile: int = 0
 
     def c(self):
         o = capi.psr_opts()
@@ -41,7 +42,15 @@ class Options:
         o.warps_per_block, o.blocks_per_sm = int(self.warps_per_block), int(self.blocks_per_sm)
         o.fold_every, o.count_pairs = int(self.fold_every), int(bool(self.count_pairs))
         o.kernel = int(self.kernel)
+        o.source_tile = int(self.source_tile)
         return o
+
+    @classmethod
+    def from_c(cls, o):
+        return cls(precision=o.precision, table_n=o.table_n, interp=o.interp, accum=o.accum,
+                   warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm,
+                   fold_every=o.fold_every, count_pairs=bool(o.count_pairs), kernel=o.kernel,
+                   source_tile=o.source_tile)
 
     @property
     def fp64(self):
@@ -182,6 +191,18 @@ class Leaves:
             capi.psr_p2p_adjoint(self._h, opts.c(), cot.data_ptr(), grad_pos.data_ptr(),
                                  grad_mass.data_ptr(), _stream_handle(stream))
         return grad_pos, grad_mass
+
+    def autotune(self, opts=None, reps=3, timeout_ms=120000, stream=None):
+        """Tile shape of the FP32 forward kernel for this leaf set
+        (psr_autotune): returns (best Options, best time in ms)."""
+        import torch
+        opts = opts or Options()
+        dev = self._dev()
+        out = torch.empty((self.n, 3), dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            best, ms = capi.psr_autotune(self._h, opts.c(), out.data_ptr(), _stream_handle(stream),
+                                         int(reps), int(timeout_ms))
+        return Options.from_c(best), ms
 
     def pair_count(self, stream=None, timeout_ms=60000):
         return capi.psr_pair_count(self._h, _stream_handle(stream), timeout_ms)

@@ -22,7 +22,7 @@ PSR_BUILD_NO_FP64 = 1
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
-           "psr_check", "psr_table",
+           "psr_check", "psr_table", "psr_autotune",
            "psr_leaves_host_arrays", "psr_free_leaves", "psr_last_error", "psr_version"]
 
 
@@ -36,7 +36,7 @@ class psr_opts(ctypes.Structure):
                 ("accum", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("fold_every", ctypes.c_int),
                 ("count_pairs", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("source_tile", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class psr_info(ctypes.Structure):
@@ -85,6 +85,8 @@ def lib():
     L.psr_p2p_forces_noalloc.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp]
     L.psr_p2p_adjoint.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, vp, vp]
     L.psr_pair_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
+    L.psr_autotune.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(psr_opts), ctypes.POINTER(ctypes.c_float)]
     L.psr_check.argtypes = [vp, vp, ctypes.c_int]
     L.psr_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
     L.psr_leaves_host_arrays.argtypes = [vp, ctypes.POINTER(psr_host_arrays)]
@@ -147,6 +149,14 @@ def psr_p2p_adjoint(h, opts, d_cot, d_gpos, d_gmass, stream):
     return check(lib().psr_p2p_adjoint(h, ctypes.byref(opts), ctypes.c_void_p(d_cot),
                                        ctypes.c_void_p(d_gpos), ctypes.c_void_p(d_gmass),
                                        ctypes.c_void_p(stream)))
+
+
+def psr_autotune(h, base, d_acc, stream, reps, timeout_ms):
+    best = psr_opts()
+    ms = ctypes.c_float()
+    check(lib().psr_autotune(h, ctypes.byref(base), ctypes.c_void_p(d_acc), ctypes.c_void_p(stream),
+                             reps, timeout_ms, ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
 
 
 def psr_pair_count(h, stream, timeout_ms):

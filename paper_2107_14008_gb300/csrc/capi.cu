@@ -43,7 +43,7 @@ int wait_stream(cudaStream_t st, int timeout_ms)
 }
 
 struct Opts {
-    int precision, table_n, interp, accum, warps, bps, fold, count, kernel;
+    int precision, table_n, interp, accum, warps, bps, fold, count, kernel, tile;
 };
 
 int check_opts(const psr_opts* o, Opts* out)
@@ -51,8 +51,11 @@ int check_opts(const psr_opts* o, Opts* out)
     psr_opts d{};
     d.precision = PSR_FP32_TABLE;
     if (!o) o = &d;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i] != 0) return fail(PSR_E_ARG, "psr_opts.reserved must be zero");
+    if (o->source_tile != 0 && o->source_tile != 64 && o->source_tile != 128 &&
+        o->source_tile != 256)
+        return fail(PSR_E_ARG, "psr_opts.source_tile must be 0, 64, 128 or 256");
     if (o->kernel < PSR_KERNEL_AUTO || o->kernel > PSR_KERNEL_PACKED)
         return fail(PSR_E_ARG, "psr_opts.kernel out of range");
     if (o->precision < PSR_FP64 || o->precision > PSR_FP32_TABLE)
@@ -71,7 +74,8 @@ int check_opts(const psr_opts* o, Opts* out)
     int fold = o->fold_every ? o->fold_every : 64;
     if (fold < 1) return fail(PSR_E_ARG, "psr_opts.fold_every must be positive");
     *out = Opts{o->precision, tn, o->interp, o->accum, w, o->blocks_per_sm, fold,
-                o->count_pairs ? 1 : 0, o->kernel == PSR_KERNEL_AUTO ? PSR_KERNEL_SCALAR : o->kernel};
+                o->count_pairs ? 1 : 0, o->kernel == PSR_KERNEL_AUTO ? PSR_KERNEL_SCALAR : o->kernel,
+                o->source_tile};
     return PSR_OK;
 }
 
@@ -90,9 +94,18 @@ constexpr int kAdjStageCap = 128;  // adjoint staged particles per warp (2 float
 // block's shared memory.
 int fwd32_smem_config(const Opts& o, int* cap)
 {
-    *cap = 256;
+    *cap = o.tile ? o.tile : 256;
     if (fwd_f32_smem(o.precision, o.interp, o.table_n, o.warps, *cap) > kSmemPerBlock)
         return fail(PSR_E_ARG, "table and staging buffers exceed shared memory; use fewer warps");
+    return PSR_OK;
+}
+
+// A staged chunk always holds at least one whole leaf.
+int check_tile(const Leaves* h, int cap)
+{
+    if (cap < h->max_leaf)
+        return fail(PSR_E_ARG, "source_tile " + std::to_string(cap) + " is below the largest leaf (" +
+                                   std::to_string(h->max_leaf) + " particles)");
     return PSR_OK;
 }
 
@@ -150,12 +163,13 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
         int occ = 0, e;
         if (adjoint)
             e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
-                              kAdjStageCap, &occ);
+                              o.tile ? o.tile : kAdjStageCap, &occ);
         else if (o.precision == PSR_FP64)
             e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
         else {
             int cap;
             if ((e = fwd32_smem_config(o, &cap))) return e;
+            if ((e = check_tile(h, cap))) return e;
             e = fwd_f32_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
                                   cap, o.kernel, &occ);
         }
@@ -185,6 +199,7 @@ int prepare_forward(Leaves* h, const psr_opts* opts, FwdArgs* a, int* precision)
     if ((rc = resolve_warps(o, fwd32))) return rc;
     *a = base_args(h, o);
     if (fwd32 && (rc = fwd32_smem_config(o, &a->stage_cap))) return rc;
+    if (fwd32 && (rc = check_tile(h, a->stage_cap))) return rc;
     if ((rc = grid_blocks(h, o, 0, &a->blocks))) return rc;
     *precision = o.precision;
     return PSR_OK;
@@ -305,6 +320,7 @@ int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stre
     FwdArgs a = base_args(h, o);
     a.out = d_acc;
     if (fwd32 && (rc = fwd32_smem_config(o, &a.stage_cap))) return rc;
+    if (fwd32 && (rc = check_tile(h, a.stage_cap))) return rc;
     if ((rc = grid_blocks(h, o, 0, &a.blocks))) return rc;
     if (o.count) {
         cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 8, st);
@@ -331,9 +347,10 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     if ((rc = ensure_table(h, o, st))) return rc;
     FwdArgs a = base_args(h, o);
     a.cot = d_cot;
-    a.stage_cap = kAdjStageCap;
+    a.stage_cap = o.tile ? o.tile : kAdjStageCap;
+    if (o.precision != PSR_FP64 && (rc = check_tile(h, a.stage_cap))) return rc;
     if (o.precision != PSR_FP64 &&
-        adj_f32_smem(o.precision, o.interp, o.table_n, o.warps, kAdjStageCap) > kSmemPerBlock)
+        adj_f32_smem(o.precision, o.interp, o.table_n, o.warps, a.stage_cap) > kSmemPerBlock)
         return fail(PSR_E_ARG, "adjoint table and staging buffers exceed shared memory; "
                                "use fewer warps or a smaller table");
     a.out = d_grad_pos;
@@ -341,6 +358,72 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     if ((rc = grid_blocks(h, o, 1, &a.blocks))) return rc;
     int e = (o.precision == PSR_FP64) ? launch_adj_f64(a, st) : launch_adj_f32(a, o.precision, st);
     if (e) return cuda_fail((cudaError_t)e, "adjoint kernel launch");
+    return PSR_OK;
+}
+
+int psr_autotune(psr_leaves* hh, const psr_opts* base, void* d_acc, void* stream, int reps,
+                 int timeout_ms, psr_opts* best, float* best_ms)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h || !d_acc || !best) return fail(PSR_E_ARG, "null argument");
+    if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
+    if (reps < 1) return fail(PSR_E_ARG, "reps must be >= 1");
+    psr_opts b{};
+    if (base) b = *base;
+    else b.precision = PSR_FP32_TABLE;
+    Opts chk;
+    int rc = check_opts(&b, &chk);
+    if (rc) return rc;
+    if (b.precision == PSR_FP64) return fail(PSR_E_ARG, "the autotuner covers the FP32 kernels");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce;
+    if ((ce = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    if ((ce = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    float best_t = -1.0f;
+    psr_opts best_o = b;
+    const int kernels[2] = {PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED};
+    const int warps[2] = {4, 8};
+    const int tiles[3] = {64, 128, 256};
+    for (int ki = 0; ki < 2 && rc == PSR_OK; ++ki)
+        for (int wi = 0; wi < 2 && rc == PSR_OK; ++wi)
+            for (int ti = 0; ti < 3 && rc == PSR_OK; ++ti) {
+                psr_opts c = b;
+                c.kernel = kernels[ki];
+                c.warps_per_block = warps[wi];
+                c.source_tile = tiles[ti];
+                c.count_pairs = 0;
+                if (tiles[ti] < h->max_leaf) continue;
+                Opts oc;
+                if (check_opts(&c, &oc) != PSR_OK) continue;
+                if (fwd_f32_smem(oc.precision, oc.interp, oc.table_n, warps[wi], tiles[ti]) >
+                    kSmemPerBlock)
+                    continue;
+                if ((rc = psr_p2p_forces(hh, &c, d_acc, stream))) break;  // warm-up
+                float tmin = -1.0f;
+                for (int r = 0; r < reps && rc == PSR_OK; ++r) {
+                    if ((ce = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventRecord"); break; }
+                    if ((rc = psr_p2p_forces(hh, &c, d_acc, stream))) break;
+                    if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventRecord"); break; }
+                    if ((rc = wait_stream(st, timeout_ms))) break;
+                    float ms = 0.0f;
+                    if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventElapsedTime"); break; }
+                    if (tmin < 0.0f || ms < tmin) tmin = ms;
+                }
+                if (rc == PSR_OK && tmin >= 0.0f && (best_t < 0.0f || tmin < best_t)) {
+                    best_t = tmin;
+                    best_o = c;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_t < 0.0f) return fail(PSR_E_ARG, "no candidate tile shape fits this leaf set");
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
     return PSR_OK;
 }
 

@@ -233,3 +233,44 @@ def test_device_calls_refuse_before_upload():
     with pytest.raises(capi.PsrError) as e:
         lv.forces()
     assert e.value.code == capi.PSR_E_STATE
+
+
+def test_options_marshal_to_the_c_struct_and_back():
+    o = psr.Options(precision=psr.PSR_FP32_EXACT, table_n=4096, interp=psr.PSR_CUBIC,
+                    accum=psr.PSR_ACC_KAHAN32, warps_per_block=4, blocks_per_sm=2, fold_every=32,
+                    count_pairs=True, kernel=psr.PSR_KERNEL_PACKED, source_tile=128)
+    c = o.c()
+    assert isinstance(c, capi.psr_opts)
+    assert (c.precision, c.table_n, c.interp, c.accum, c.warps_per_block, c.blocks_per_sm,
+            c.fold_every, c.count_pairs, c.kernel, c.source_tile) == (1, 4096, 1, 1, 4, 2, 32, 1, 2,
+                                                                       128)
+    assert list(c.reserved) == [0] * len(c.reserved)
+    assert psr.Options.from_c(c) == o
+
+
+def test_ctypes_struct_layouts_match_the_header(tmp_path):
+    """Compile a C probe against include/psr.h and compare sizes and offsets
+    with the ctypes mirrors used by the binding."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    structs = {"psr_box": capi.psr_box, "psr_opts": capi.psr_opts, "psr_info": capi.psr_info,
+               "psr_host_arrays": capi.psr_host_arrays}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "psr.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[name + "." + fname]) == getattr(cls, fname).offset, (name, fname)

@@ -323,3 +323,82 @@ def test_autograd_function_backward_is_adjoint():
                                     b.G, cells=True)
     assert rel_rms(pos.grad.cpu().numpy(), gx_ref) < 1e-6
     assert rel_rms(mass.grad.cpu().numpy(), gm_ref) < 1e-6
+
+
+# -------------------------------------------------------- tiles, autotune ---
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("tile", [64, 128, 256])
+def test_source_tile_sizes(kernel, tile):
+    b = CASES["clustered"]()
+    ref, _, _ = oracle_acc(b, "clustered")
+    acc, _ = gpu_forces(b, psr.Options(kernel=kernel, source_tile=tile), 32)
+    assert rel_rms(acc, ref) < 2e-5
+    cot = synth.cotangent(b.n, 5)
+    gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(source_tile=tile))
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4
+    assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5
+
+
+def test_source_tile_values_are_checked():
+    b = CASES["uniform"]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    for bad in (32, 100, 512):
+        with pytest.raises(capi.PsrError) as e:
+            lv.forces(psr.Options(source_tile=bad))
+        assert e.value.code == capi.PSR_E_ARG
+
+
+def test_autotune_picks_a_valid_tile_shape():
+    b = CASES["clustered"]()
+    ref, _, _ = oracle_acc(b, "clustered")
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    best, ms = lv.autotune(psr.Options(), reps=2)
+    assert ms > 0
+    assert best.kernel in KERNELS and best.warps_per_block in (4, 8)
+    assert best.source_tile in (64, 128, 256)
+    acc = lv.forces(best).double().cpu().numpy()
+    assert rel_rms(acc, ref) < 2e-5
+
+
+# ------------------------------------------------------- batched workload ---
+
+def test_batch_workload_graph_replay_sampled():
+    """64 boxes, N log-uniform in [8^3, 64^3], L in [50, 400], half uniform and
+    half NFW-clustered: one persistent launch, autotuned, replayed from a CUDA
+    graph; every box checked against the oracle on sampled targets."""
+    boxes = synth.batch()
+    lv = psr.Leaves.build_batch([(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G) for b in boxes],
+                                max_leaf=32).upload()
+    best, _ = lv.autotune(psr.Options(), reps=1)
+    out = torch.zeros((lv.n, 3), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lv.forces(best, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    eager = out.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lv.forces(best, out=out)
+    out.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    lv.check()
+    acc = out.double().cpu().numpy()
+    off = 0
+    rng = np.random.default_rng(31)
+    num = den = 0.0
+    for b in boxes:
+        tg = np.sort(rng.choice(b.n, min(200, b.n), replace=False))
+        ref, _, _ = oracle.forces(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, targets=tg, cells=True)
+        d = acc[off + tg] - ref
+        assert rel_rms(acc[off + tg], ref) < 5e-5, b.name
+        num += np.sum(d * d)
+        den += np.sum(ref * ref)
+        off += b.n
+    assert np.sqrt(num / den) < 2e-5
