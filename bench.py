@@ -58,6 +58,15 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (the job's time is the slowest
+    rank's)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -323,9 +332,7 @@ def run_psr(args):
     ms = [a.elapsed_time(e) for a, e in evs]
     total_ms = sum(ms)
     if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, pg, dev)
     lv.check()
     acc32 = acc.double().cpu().numpy()
     # within-cutoff pairs (untimed counting run, after the timed region)

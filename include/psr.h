@@ -94,7 +94,15 @@ typedef struct {
     int source_tile;     /* FP32 kernels: source particles staged per warp in
                             shared memory, 64 | 128 | 256 and >= the largest
                             leaf; 0 = default (forward 256, adjoint 128)    */
-    int reserved[6];     /* must be zero                                      */
+    int shard_count;     /* split the target leaves over shard_count launches
+                            (one per GPU, inputs replicated): this launch
+                            computes the targets of schedule entries
+                            shard_index, shard_index + shard_count, ... (the
+                            schedule is largest-work first, so the shards are
+                            balanced) and leaves every other output element
+                            untouched; 0 or 1 = all targets                  */
+    int shard_index;     /* 0 <= shard_index < max(shard_count, 1)          */
+    int reserved[4];     /* must be zero                                      */
 } psr_opts;
 
 typedef struct {

@@ -34,6 +34,8 @@ class Options:
     count_pairs: bool = False
     kernel: int = 0
     source_tile: int = 0
+    shard_count: int = 0
+    shard_index: int = 0
 
     def c(self):
         o = capi.psr_opts()
@@ -43,6 +45,7 @@ class Options:
         o.fold_every, o.count_pairs = int(self.fold_every), int(bool(self.count_pairs))
         o.kernel = int(self.kernel)
         o.source_tile = int(self.source_tile)
+        o.shard_count, o.shard_index = int(self.shard_count), int(self.shard_index)
         return o
 
     @classmethod
@@ -50,7 +53,8 @@ class Options:
         return cls(precision=o.precision, table_n=o.table_n, interp=o.interp, accum=o.accum,
                    warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm,
                    fold_every=o.fold_every, count_pairs=bool(o.count_pairs), kernel=o.kernel,
-                   source_tile=o.source_tile)
+                   source_tile=o.source_tile, shard_count=o.shard_count,
+                   shard_index=o.shard_index)
 
     @property
     def fp64(self):
@@ -138,6 +142,15 @@ class Leaves:
                "items": v(a.items, (nl,))}
         out["pd"] = v(a.pd, (self.n, 4)) if bool(a.pd) else None
         return out
+
+    def shard_targets(self, shard_count, shard_index):
+        """Sorted-order indices of the particles a launch with this shard
+        computes (the host mirror of the kernels' item assignment)."""
+        A = self.host_arrays()
+        items = A["items"][shard_index::max(1, shard_count)]
+        leaf = A["leaf"]
+        return np.concatenate([np.arange(leaf[i, 0], leaf[i, 0] + leaf[i, 1]) for i in items]) \
+            if len(items) else np.zeros(0, dtype=np.int64)
 
     @property
     def evaluated_pairs(self):

@@ -36,7 +36,8 @@ class psr_opts(ctypes.Structure):
                 ("accum", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("fold_every", ctypes.c_int),
                 ("count_pairs", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("source_tile", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("source_tile", ctypes.c_int), ("shard_count", ctypes.c_int),
+                ("shard_index", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class psr_info(ctypes.Structure):

@@ -43,7 +43,7 @@ int wait_stream(cudaStream_t st, int timeout_ms)
 }
 
 struct Opts {
-    int precision, table_n, interp, accum, warps, bps, fold, count, kernel, tile;
+    int precision, table_n, interp, accum, warps, bps, fold, count, kernel, tile, nshard, shard;
 };
 
 int check_opts(const psr_opts* o, Opts* out)
@@ -51,8 +51,11 @@ int check_opts(const psr_opts* o, Opts* out)
     psr_opts d{};
     d.precision = PSR_FP32_TABLE;
     if (!o) o = &d;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i] != 0) return fail(PSR_E_ARG, "psr_opts.reserved must be zero");
+    const int nshard = o->shard_count > 1 ? o->shard_count : 1;
+    if (o->shard_count < 0 || o->shard_index < 0 || o->shard_index >= nshard)
+        return fail(PSR_E_ARG, "psr_opts.shard_index must be in [0, shard_count)");
     if (o->source_tile != 0 && o->source_tile != 64 && o->source_tile != 128 &&
         o->source_tile != 256)
         return fail(PSR_E_ARG, "psr_opts.source_tile must be 0, 64, 128 or 256");
@@ -75,7 +78,7 @@ int check_opts(const psr_opts* o, Opts* out)
     if (fold < 1) return fail(PSR_E_ARG, "psr_opts.fold_every must be positive");
     *out = Opts{o->precision, tn, o->interp, o->accum, w, o->blocks_per_sm, fold,
                 o->count_pairs ? 1 : 0, o->kernel == PSR_KERNEL_AUTO ? PSR_KERNEL_SCALAR : o->kernel,
-                o->source_tile};
+                o->source_tile, nshard, o->shard_index};
     return PSR_OK;
 }
 
@@ -139,6 +142,8 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     a.warps_per_block = o.warps;
     a.max_leaf = h->max_leaf;
     a.variant = o.kernel;
+    a.item_stride = o.nshard;
+    a.item_offset = o.shard;
     return a;
 }
 

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
     unsigned long long npairs = 0;
     for (;;) {
         int it = 0;
-        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketFwd, 1u);
+        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketFwd, 1u) * a.item_stride + a.item_offset;
         it = __shfl_sync(kFull, it, 0);
         if (it >= a.n_items) break;
         int I = a.items[it];

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     for (;;) {
         int it = 0;
-        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketAdj, 1u);
+        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketAdj, 1u) * a.item_stride + a.item_offset;
         it = __shfl_sync(kFull, it, 0);
         if (it >= a.n_items) break;
         int I = a.items[it];
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) p2p_adj_f64_kernel(const FwdArgs a)
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     for (;;) {
         int it = 0;
-        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketAdj, 1u);
+        if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketAdj, 1u) * a.item_stride + a.item_offset;
         it = __shfl_sync(kFull, it, 0);
         if (it >= a.n_items) break;
         int I = a.items[it];

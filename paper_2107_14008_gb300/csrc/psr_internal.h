@@ -142,7 +142,9 @@ struct FwdArgs {
     int blocks;
     int max_leaf;
     int variant;     // FP32 forward: PSR_KERNEL_SCALAR or PSR_KERNEL_PACKED
-    int stage_cap;   // FP32 forward: staged particles per warp
+    int stage_cap;   // FP32 kernels: staged particles per warp
+    int item_stride; // this launch takes schedule entries ticket * stride + offset
+    int item_offset;
 };
 
 int launch_table(int table_n, int interp, double x_c, void* d_out, void* d_q_out, void* stream);

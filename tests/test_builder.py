@@ -238,12 +238,13 @@ def test_device_calls_refuse_before_upload():
 def test_options_marshal_to_the_c_struct_and_back():
     o = psr.Options(precision=psr.PSR_FP32_EXACT, table_n=4096, interp=psr.PSR_CUBIC,
                     accum=psr.PSR_ACC_KAHAN32, warps_per_block=4, blocks_per_sm=2, fold_every=32,
-                    count_pairs=True, kernel=psr.PSR_KERNEL_PACKED, source_tile=128)
+                    count_pairs=True, kernel=psr.PSR_KERNEL_PACKED, source_tile=128,
+                    shard_count=3, shard_index=2)
     c = o.c()
     assert isinstance(c, capi.psr_opts)
     assert (c.precision, c.table_n, c.interp, c.accum, c.warps_per_block, c.blocks_per_sm,
-            c.fold_every, c.count_pairs, c.kernel, c.source_tile) == (1, 4096, 1, 1, 4, 2, 32, 1, 2,
-                                                                       128)
+            c.fold_every, c.count_pairs, c.kernel, c.source_tile, c.shard_count,
+            c.shard_index) == (1, 4096, 1, 1, 4, 2, 32, 1, 2, 128, 3, 2)
     assert list(c.reserved) == [0] * len(c.reserved)
     assert psr.Options.from_c(c) == o
 
