@@ -51,10 +51,13 @@ def parse():
     p.add_argument("--cpu-targets", type=int, default=100000,
                    help="targets in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="precision", choices=["precision", "precision96", "adjoint64"],
+    p.add_argument("--workload", default="precision",
+                   choices=["precision", "precision96", "adjoint64", "large"],
                    help="precision: 128^3 NFW, L=500 (the headline); adjoint64: 64^3 NFW, L=200 "
                         "(a small case of the same kernels for profiling); precision96: 96^3 at "
-                        "the same density and halo fraction as precision")
+                        "the same density and halo fraction as precision; large: 512^3, "
+                        "L=1000, N_PM=512, 70%% of the mass in 200000 halos, leaves <= 64 "
+                        "(FP32 paths only)")
     return p.parse_args()
 
 
@@ -271,16 +274,19 @@ def make_box(args, rank=0):
     import synth
     if args.workload == "adjoint64":
         return synth.adjoint(seed=12348 + rank)
+    if args.workload == "large":
+        return synth.large(seed=12349 + rank)
     if args.workload == "precision96":
         return synth.precision(seed=12346 + rank, nside=96, L=375.0, n_halos=1688)
     return synth.precision(seed=12346 + rank)
 
 
 def workload_config(b, args):
-    return {"workload": "NFW-clustered %d^3, L=%g, N_PM=%d, 60%% mass in %d halos, "
-                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=32"
-                        % (b.n_pm, b.L, b.n_pm, b.meta.get("n_halos", 0)),
-            "n": b.n, "L": b.L, "r_s": b.r_s, "r_c": b.r_c, "max_leaf": 32,
+    frac = 70 if args.workload == "large" else 60
+    return {"workload": "NFW-clustered %d^3, L=%g, N_PM=%d, %d%% mass in %d halos, "
+                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=%d"
+                        % (b.n_pm, b.L, b.n_pm, frac, b.meta.get("n_halos", 0), b.max_leaf),
+            "n": b.n, "L": b.L, "r_s": b.r_s, "r_c": b.r_c, "max_leaf": b.max_leaf,
             "path": "FP32 pair math, T from a %d-interval %s table in shared memory, %s "
                     "accumulation" % (args.table_n, args.interp, args.accum),
             "l2": "flushed between timed steps (256 MB write)"}
@@ -302,7 +308,8 @@ def run_psr(args):
         pg = dist
     b = make_box(args, rank)
     t0 = time.perf_counter()
-    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
+                          fp64=args.fp64_steps > 0)
     build_s = time.perf_counter() - t0
     lv.upload(dev)
     info = lv.info
@@ -428,7 +435,8 @@ def run_psr(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            lv2 = psr.Leaves.build(pos_h.numpy(), b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
+            lv2 = psr.Leaves.build(pos_h.numpy(), b.mass, b.L, b.r_s, b.r_c, b.G,
+                                   max_leaf=b.max_leaf, fp64=False)
             lv2.upload(dev)
             out_h.copy_(lv2.forces(opts))
             torch.cuda.synchronize()
