@@ -132,13 +132,15 @@ typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
  * pack, Section 2), and build the near-field leaf-pair list grouped by
  * target leaf (the TaskGroup/GroupIdx of Section 3.2) with a periodic image
  * code per entry.
- *   pos      host, n x 3 FP64, any real values (wrapped into [0, L))
+ *   pos      host, n x 3 FP64, any real values (wrapped into [0, L));
+ *            may be NULL when n = 0
  *   mass     host, n FP64, or NULL for equal masses 1/n
  *   box      host, box parameters
  *   max_leaf 1..64
  *   flags    PSR_BUILD_* bits
  *   out      receives the handle; free with psr_free_leaves
- * Errors: PSR_E_ARG (NULL, n < 1, n >= 2^31, non-finite input, max_leaf out
+ * n = 0 gives an empty handle: the device calls then do nothing.
+ * Errors: PSR_E_ARG (NULL, n < 0, n >= 2^31, non-finite input, max_leaf out
  * of range, r_s <= 0), PSR_E_CUTOFF (r_c <= 0 or r_c >= L), PSR_E_NOMEM.
  */
 int psr_build_leaves(const double* pos, const double* mass, int64_t n, const psr_box* box,

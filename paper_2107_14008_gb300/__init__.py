@@ -109,7 +109,8 @@ class Leaves:
         keep, pp, mm, ns, bx = [], [], [], [], []
         for (pos, mass, L, r_s, r_c, G) in boxes:
             p = _host_f64(pos, 3)
-            m = _host_f64(mass, 1) if mass is not None else np.full(p.shape[0], 1.0 / p.shape[0])
+            m = _host_f64(mass, 1) if mass is not None else \
+                np.full(p.shape[0], 1.0 / max(p.shape[0], 1))
             keep += [p, m]
             pp.append(p.ctypes.data_as(dp))
             mm.append(m.ctypes.data_as(dp))
@@ -128,6 +129,8 @@ class Leaves:
 
     @property
     def perm(self):
+        if self.n == 0:
+            return np.zeros(0, dtype=np.int64)
         return np.ctypeslib.as_array(self._info.perm, shape=(self.n,)).copy()
 
     def host_arrays(self):
@@ -135,7 +138,10 @@ class Leaves:
         a = capi.psr_leaves_host_arrays(self._h)
         inf = self._info
         nl, npairs = int(inf.n_leaves), int(inf.n_pairs)
-        v = lambda p, shape: np.ctypeslib.as_array(p, shape=shape).copy()
+        def v(p, shape):
+            if shape[0] == 0 or not bool(p):
+                return np.zeros(shape, dtype=np.dtype(p._type_))
+            return np.ctypeslib.as_array(p, shape=shape).copy()
         out = {"pf": v(a.pf, (self.n, 4)), "leaf": v(a.leaf, (nl, 4)), "lcen": v(a.lcen, (nl, 4)),
                "rowptr": v(a.rowptr, (nl + 1,)),
                "pairs": v(a.pairs, (npairs,)) if npairs else np.zeros(0, np.uint32),

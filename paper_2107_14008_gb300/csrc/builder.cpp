@@ -285,8 +285,8 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
     double ratio = -1.0;
     for (int b = 0; b < nbox; ++b) {
         const psr_box& bx = boxes[b];
-        if (!pos[b] || n[b] < 1) {
-            *err = "box " + std::to_string(b) + ": null positions or n < 1";
+        if (n[b] < 0 || (n[b] > 0 && !pos[b])) {
+            *err = "box " + std::to_string(b) + ": null positions or n < 0";
             return PSR_E_ARG;
         }
         if (!(std::isfinite(bx.L) && bx.L > 0) || !(std::isfinite(bx.r_s) && bx.r_s > 0) ||
@@ -402,6 +402,7 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
             t.base = h->box_first[b];
             t.max_leaf = max_leaf;
             t.leaf_base = leaf_total;
+            if (n[b] == 0) continue;  // an empty box has no leaves
             t.root = t.build(0, n[b], 0, 0, 0, 0);
             leaf_total += (int32_t)t.leaves.size();
             if (leaf_total >= (1 << 27)) {

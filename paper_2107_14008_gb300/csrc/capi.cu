@@ -311,11 +311,12 @@ int psr_upload(psr_leaves* hh, void* d_ws, size_t bytes, void* stream)
 int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stream)
 {
     Leaves* h = reinterpret_cast<Leaves*>(hh);
-    if (!h || !d_acc) return fail(PSR_E_ARG, "null argument");
+    if (!h || (!d_acc && h->n > 0)) return fail(PSR_E_ARG, "null argument");
     if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
     Opts o;
     int rc = check_opts(opts, &o);
     if (rc) return rc;
+    if (h->n == 0) return PSR_OK;  // nothing to compute
     if (o.precision == PSR_FP64 && h->pd.empty())
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     cudaStream_t st = (cudaStream_t)stream;
@@ -340,11 +341,12 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
                     void* d_grad_mass, void* stream)
 {
     Leaves* h = reinterpret_cast<Leaves*>(hh);
-    if (!h || !d_cot || !d_grad_pos) return fail(PSR_E_ARG, "null argument");
+    if (!h || ((!d_cot || !d_grad_pos) && h->n > 0)) return fail(PSR_E_ARG, "null argument");
     if (!h->uploaded) return fail(PSR_E_STATE, "psr_upload has not been called");
     Opts o;
     int rc = check_opts(opts, &o);
     if (rc) return rc;
+    if (h->n == 0) return PSR_OK;  // nothing to compute
     if (o.precision == PSR_FP64 && h->pd.empty())
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     cudaStream_t st = (cudaStream_t)stream;

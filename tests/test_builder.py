@@ -275,3 +275,23 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(got[name + "." + fname]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_empty_inputs():
+    """An empty box gives an empty handle; an empty box inside a batch adds
+    no leaves and no pairs and does not disturb its neighbours."""
+    e = psr.Leaves.build(np.zeros((0, 3)), None, 10.0, 1.0, 4.5)
+    assert (e.n, e.info.n_leaves, e.info.n_pairs, e.evaluated_pairs) == (0, 0, 0, 0)
+    assert e.perm.size == 0
+    b1, b2 = synth.small(nside=8), synth.small(nside=10)
+    parts = [(b1.pos, b1.mass, b1.L, b1.r_s, b1.r_c, 1.0),
+             (np.zeros((0, 3)), None, 50.0, 0.5 * b1.r_s, 0.5 * b1.r_c, 1.0),
+             (b2.pos, b2.mass, b2.L, b2.r_s, b2.r_c, 1.0)]
+    lv = psr.Leaves.build_batch(parts, max_leaf=16)
+    one = psr.Leaves.build_batch([parts[0], parts[2]], max_leaf=16)
+    assert lv.n == b1.n + b2.n and lv.info.nbox == 3
+    A, B = lv.host_arrays(), one.host_arrays()
+    np.testing.assert_array_equal(A["pairs"], B["pairs"])
+    np.testing.assert_array_equal(A["pf"], B["pf"])
+    assert np.all(A["leaf"][:, 2] != 1)  # no leaf belongs to the empty box
+    np.testing.assert_array_equal(np.sort(lv.perm), np.arange(lv.n))

@@ -430,3 +430,22 @@ def test_shards_run_in_sequence_reproduce_the_full_launch(precision, nshard):
     torch.cuda.synchronize()
     assert torch.equal(gp, g_full) and torch.equal(gm, m_full)
     lv.check()
+
+
+def test_empty_handle_and_empty_box_in_a_batch():
+    e = psr.Leaves.build(np.zeros((0, 3)), None, 10.0, 1.0, 4.5).upload()
+    for prec in (psr.PSR_FP64, psr.PSR_FP32_TABLE):
+        assert e.forces(psr.Options(precision=prec)).shape == (0, 3)
+        gx, gm = e.adjoint(torch.zeros((0, 3)), psr.Options(precision=prec))
+        assert gx.shape == (0, 3) and gm.shape == (0,)
+    e.check()
+    b1, b2 = _clustered(n=1500), _small_box()
+    parts = [(b1.pos, b1.mass, b1.L, b1.r_s, b1.r_c, b1.G),
+             (np.zeros((0, 3)), None, 40.0, b1.r_s, b1.r_c, 1.0),
+             (b2.pos, b2.mass, b2.L, b2.r_s, b2.r_c, b2.G)]
+    lv = psr.Leaves.build_batch(parts).upload()
+    acc = lv.forces(psr.Options()).cpu().numpy()
+    a1, _ = gpu_forces(b1, psr.Options())
+    a2, _ = gpu_forces(b2, psr.Options())
+    np.testing.assert_array_equal(acc[:b1.n], a1.astype(np.float32))
+    np.testing.assert_array_equal(acc[b1.n:], a2.astype(np.float32))
