@@ -117,7 +117,8 @@ typedef struct {
     int max_row;             /* most source leaves of one target leaf          */
     double build_seconds;    /* host time of psr_build_leaves*                 */
     const int64_t* perm;     /* host, n: sorted index -> original index
-                                (owned by the handle)                          */
+                                (owned by the handle); NULL for a handle built
+                                on the device                                  */
 } psr_info;
 
 typedef struct psr_leaves psr_leaves; /* opaque, host-owned */

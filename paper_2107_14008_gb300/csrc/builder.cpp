@@ -251,7 +251,7 @@ Layout make_layout(const Leaves& h)
 {
     Layout L{};
     size_t o = 0;
-    const size_t n = (size_t)h.n, nl = h.leaf.size() / 4, np = h.pairs.size();
+    const size_t n = (size_t)h.n, nl = (size_t)h.n_leaves, np = (size_t)h.n_pairs;
     L.pf = o;        o = align256(o + n * 16);
     L.pd = o;        o = align256(o + ((h.flags & PSR_BUILD_NO_FP64) ? 0 : n * 32));
     L.perm = o;      o = align256(o + n * 4);
@@ -259,7 +259,7 @@ Layout make_layout(const Leaves& h)
     L.lcen = o;      o = align256(o + nl * 16);
     L.rowptr = o;    o = align256(o + (nl + 1) * 8);
     L.pairs = o;     o = align256(o + np * 4);
-    L.items = o;     o = align256(o + h.items.size() * 4);
+    L.items = o;     o = align256(o + nl * 4);
     L.boxes = o;     o = align256(o + h.boxdev.size() * sizeof(BoxDev));
     L.table = o;     o = align256(o + 2 * (size_t)(kMaxTableN + 1) * 16);
     L.cotf = o;      o = align256(o + n * ((h.flags & PSR_BUILD_NO_FP64) ? 16 : 32));
@@ -554,6 +554,9 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
         for (int64_t g = 0; g < nl; ++g) h->items[g] = (int32_t)g;
         std::stable_sort(h->items.begin(), h->items.end(),
                          [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+        h->n_leaves = nl;
+        h->n_pairs = (int64_t)h->pairs.size();
+        h->has_pd = !(flags & PSR_BUILD_NO_FP64);
         h->lay = make_layout(*h);
     } catch (const std::bad_alloc&) {
         delete h;

@@ -118,7 +118,7 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     char* w = h->d_ws;
     const Layout& L = h->lay;
     a.pf = w + L.pf;
-    a.pd = h->pd.empty() ? nullptr : w + L.pd;
+    a.pd = h->has_pd ? w + L.pd : nullptr;
     a.perm = reinterpret_cast<const int32_t*>(w + L.perm);
     a.leaf = reinterpret_cast<const int32_t*>(w + L.leaf);
     a.lcen = reinterpret_cast<const int32_t*>(w + L.lcen);
@@ -130,9 +130,9 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     a.ctrl = reinterpret_cast<unsigned*>(w + L.ctrl);
     a.cot_sorted = w + L.cotf;
     a.n = h->n;
-    a.n_leaves = (int64_t)(h->leaf.size() / 4);
-    a.n_pairs = (int64_t)h->pairs.size();
-    a.n_items = (int)h->items.size();
+    a.n_leaves = h->n_leaves;
+    a.n_pairs = h->n_pairs;
+    a.n_items = (int)h->n_leaves;
     a.nbox = h->nbox;
     a.table_n = o.table_n;
     a.interp = o.interp;
@@ -198,7 +198,7 @@ int prepare_forward(Leaves* h, const psr_opts* opts, FwdArgs* a, int* precision)
     Opts o;
     int rc = check_opts(opts, &o);
     if (rc) return rc;
-    if (o.precision == PSR_FP64 && h->pd.empty())
+    if (o.precision == PSR_FP64 && !h->has_pd)
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     const bool fwd32 = o.precision != PSR_FP64;
     if ((rc = resolve_warps(o, fwd32))) return rc;
@@ -251,16 +251,16 @@ int psr_leaves_info(const psr_leaves* hh, psr_info* info)
     if (!h || !info) return fail(PSR_E_ARG, "null argument");
     std::memset(info, 0, sizeof *info);
     info->n = h->n;
-    info->n_leaves = (int64_t)(h->leaf.size() / 4);
-    info->n_pairs = (int64_t)h->pairs.size();
-    info->n_items = (int64_t)h->items.size();
+    info->n_leaves = h->n_leaves;
+    info->n_pairs = h->n_pairs;
+    info->n_items = h->n_leaves;
     info->nbox = h->nbox;
     info->evaluated_pairs = h->evaluated;
     info->device_bytes = h->lay.total;
     info->max_leaf = h->max_leaf;
     info->max_row = h->max_row;
     info->build_seconds = h->build_seconds;
-    info->perm = h->perm.data();
+    info->perm = h->device_built ? nullptr : h->perm.data();
     return PSR_OK;
 }
 
@@ -317,7 +317,7 @@ int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stre
     int rc = check_opts(opts, &o);
     if (rc) return rc;
     if (h->n == 0) return PSR_OK;  // nothing to compute
-    if (o.precision == PSR_FP64 && h->pd.empty())
+    if (o.precision == PSR_FP64 && !h->has_pd)
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     cudaStream_t st = (cudaStream_t)stream;
     const bool fwd32 = o.precision != PSR_FP64;
@@ -347,7 +347,7 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     int rc = check_opts(opts, &o);
     if (rc) return rc;
     if (h->n == 0) return PSR_OK;  // nothing to compute
-    if (o.precision == PSR_FP64 && h->pd.empty())
+    if (o.precision == PSR_FP64 && !h->has_pd)
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = resolve_warps(o, false))) return rc;
@@ -490,8 +490,9 @@ int psr_leaves_host_arrays(const psr_leaves* hh, psr_host_arrays* out)
 {
     const Leaves* h = reinterpret_cast<const Leaves*>(hh);
     if (!h || !out) return fail(PSR_E_ARG, "null argument");
+    if (h->device_built) return fail(PSR_E_STATE, "a device-built handle has no host arrays");
     out->pf = h->pf.data();
-    out->pd = h->pd.empty() ? nullptr : h->pd.data();
+    out->pd = !h->has_pd ? nullptr : h->pd.data();
     out->leaf = h->leaf.data();
     out->lcen = h->lcen.data();
     out->rowptr = h->rowptr.data();

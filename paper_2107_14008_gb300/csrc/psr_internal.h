@@ -94,6 +94,11 @@ struct Leaves {
     int64_t evaluated = 0;
     int max_leaf = 0;
     int max_row = 0;
+    // counts (set by both builders; a device-built handle has no host arrays)
+    int64_t n_leaves = 0;
+    int64_t n_pairs = 0;
+    bool has_pd = false;        // FP64 payload present in the workspace
+    bool device_built = false;  // arrays were built on the device
     // device state
     Layout lay{};
     char* d_ws = nullptr;
