@@ -294,6 +294,63 @@ typedef struct {
 } psr_host_arrays;
 int psr_leaves_host_arrays(const psr_leaves* h, psr_host_arrays* out);
 
+/*
+ * psr_leaves_regions - host: byte offsets of the arrays inside the device
+ * workspace, with the layouts of psr_host_arrays, plus perm (n int32: sorted
+ * index -> original index) and the workspace size.  pd is meaningful only
+ * without PSR_BUILD_NO_FP64.  For reading a workspace on the device, e.g.
+ * the permutation of a device-built handle.  Errors: PSR_E_ARG (NULL).
+ */
+typedef struct {
+    size_t pf, pd, perm, leaf, lcen, rowptr, pairs, items, total;
+} psr_regions;
+int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
+
+/* ------------------------------------------------- device leaf builder */
+/*
+ * The leaf set of psr_build_leaves built on the GPU from device-resident
+ * positions (one box): the same leaves, pair list and schedule, bit for bit
+ * (paper, Section 2 and Section 3.2; the tree is a binary radix tree over
+ * the Morton-ordered leaf cells, whose walk keeps the same leaf pairs in the
+ * same order as the host's octree walk).  Two calls, so that the caller can
+ * size the workspace from the counts:
+ *
+ * psr_device_build_scratch_bytes - host: scratch bytes psr_device_build
+ * needs for n particles (about 230 per particle).  Errors: PSR_E_ARG
+ * (n < 1 or n > 2^28, NULL).
+ *
+ * psr_device_build - enqueue key, radix sort, leaf, radix tree and pair
+ * count kernels on cuda_stream, wait for them (each wait at most timeout_ms;
+ * <= 0 means 60 s) and read back the leaf and pair counts; returns a handle
+ * whose workspace is not yet written (psr_leaves_info works on it).
+ *   d_pos     device, n x 3 FP64, any real values (wrapped into [0, L));
+ *             consumed before the call returns
+ *   d_mass    device, n FP64, or NULL for equal masses 1/n; consumed before
+ *             the call returns
+ *   n         1 .. 2^28
+ *   d_scratch device, >= psr_device_build_scratch_bytes(n) bytes, 256-byte
+ *             aligned, owned by the caller; it holds the build state until
+ *             the work psr_device_build_finish enqueues has run
+ * Not capturable in a CUDA graph (it waits on the stream).  Errors:
+ * PSR_E_ARG (argument, non-finite position or mass), PSR_E_CUTOFF,
+ * PSR_E_WORKSPACE (scratch missing, small or misaligned), PSR_E_CUDA,
+ * PSR_E_TIMEOUT, PSR_E_DEVICE (a tree bound check fired: traversal stack
+ * overflow or a malformed tree; the build is abandoned), PSR_E_NOMEM.
+ *
+ * psr_device_build_finish - enqueue on cuda_stream the kernels that write
+ * the workspace (psr_leaves_info().device_bytes, 256-byte aligned, owned by
+ * the caller) from the scratch; afterwards the handle is as after
+ * psr_upload.  On a device-built handle psr_upload and
+ * psr_leaves_host_arrays return PSR_E_STATE and psr_info.perm is NULL (the
+ * permutation is in the workspace at psr_leaves_regions().perm).  Errors:
+ * PSR_E_STATE (no pending device build), PSR_E_WORKSPACE, PSR_E_CUDA.
+ */
+int psr_device_build_scratch_bytes(int64_t n, size_t* bytes);
+int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const psr_box* box,
+                     int max_leaf, int flags, void* d_scratch, size_t scratch_bytes,
+                     void* cuda_stream, int timeout_ms, psr_leaves** out);
+int psr_device_build_finish(psr_leaves* h, void* d_ws, size_t bytes, void* cuda_stream);
+
 /* psr_free_leaves - host: free a handle (NULL is ignored). */
 void psr_free_leaves(psr_leaves* h);
 

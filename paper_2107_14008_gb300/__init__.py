@@ -122,16 +122,83 @@ class Leaves:
                                         int(max_leaf), 0 if fp64 else capi.PSR_BUILD_NO_FP64)
         return cls(h, int(sum(ns)))
 
+    @classmethod
+    def device_build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, stream=None,
+                     timeout_ms=60000):
+        """Build on the GPU from device tensors (psr_device_build and
+        psr_device_build_finish): pos (n,3) and mass (n,) or None, on one CUDA
+        device.  The result is already resident (no upload())."""
+        import torch
+        if not (hasattr(pos, "is_cuda") and pos.is_cuda):
+            raise ValueError("device_build takes CUDA tensors")
+        dev = pos.device
+        p = pos.detach().to(torch.float64).contiguous().reshape(-1, 3)
+        n = p.shape[0]
+        m = None
+        if mass is not None:
+            m = mass.detach().to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
+            if m.shape[0] != n:
+                raise ValueError("mass and pos lengths differ")
+        with torch.cuda.device(dev):
+            st = _stream_handle(stream)
+            nbytes = capi.psr_device_build_scratch_bytes(n)
+            scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            h = capi.psr_device_build(p.data_ptr(), 0 if m is None else m.data_ptr(), n,
+                                      _box(L, r_s, r_c, G), int(max_leaf),
+                                      0 if fp64 else capi.PSR_BUILD_NO_FP64, scratch.data_ptr(),
+                                      nbytes, st, int(timeout_ms))
+            lv = cls(h, n)
+            lv.workspace = torch.empty(int(lv._info.device_bytes), dtype=torch.uint8, device=dev)
+            capi.psr_device_build_finish(h, lv.workspace.data_ptr(), lv.workspace.numel(), st)
+            if stream is not None:  # the scratch is read by work queued on `stream`
+                scratch.record_stream(stream)
+            del scratch
+        return lv
+
     # -- host-side information -------------------------------------------
     @property
     def info(self):
         return self._info
 
     @property
+    def device_built(self):
+        return self.n > 0 and not bool(self._info.perm)
+
+    @property
     def perm(self):
         if self.n == 0:
             return np.zeros(0, dtype=np.int64)
+        if self.device_built:
+            r = capi.psr_leaves_regions(self._h)
+            return self.workspace[r.perm:r.perm + 4 * self.n].view(
+                __import__("torch").int32).cpu().numpy().astype(np.int64)
         return np.ctypeslib.as_array(self._info.perm, shape=(self.n,)).copy()
+
+    def device_arrays(self):
+        """Copies (numpy) of the workspace arrays, with the names and layouts
+        of host_arrays() plus perm; needs the workspace to be written."""
+        import torch
+        if self.workspace is None:
+            raise PsrError(capi.PSR_E_STATE, "the workspace has not been written")
+        torch.cuda.synchronize(self.workspace.device)
+        r = capi.psr_leaves_regions(self._h)
+        inf = self._info
+        n, nl, npairs = self.n, int(inf.n_leaves), int(inf.n_pairs)
+        ws = self.workspace
+
+        def v(off, count, dt, shape):
+            nb = count * torch.empty(0, dtype=dt).element_size()
+            return ws[off:off + nb].view(dt).cpu().numpy().reshape(shape)
+        out = {"pf": v(r.pf, 4 * n, torch.float32, (n, 4)),
+               "perm": v(r.perm, n, torch.int32, (n,)),
+               "leaf": v(r.leaf, 4 * nl, torch.int32, (nl, 4)),
+               "lcen": v(r.lcen, 4 * nl, torch.int32, (nl, 4)),
+               "rowptr": v(r.rowptr, nl + 1, torch.int64, (nl + 1,)),
+               "pairs": v(r.pairs, npairs, torch.int32, (npairs,)).view(np.uint32),
+               "items": v(r.items, nl, torch.int32, (nl,))}
+        has_pd = n > 0 and r.perm - r.pd >= 32 * n  # the FP64 region is empty without it
+        out["pd"] = v(r.pd, 4 * n, torch.float64, (n, 4)) if has_pd else None
+        return out
 
     def host_arrays(self):
         """Copies of the host arrays psr_upload sends (see psr_leaves_host_arrays)."""
@@ -152,7 +219,7 @@ class Leaves:
     def shard_targets(self, shard_count, shard_index):
         """Sorted-order indices of the particles a launch with this shard
         computes (the host mirror of the kernels' item assignment)."""
-        A = self.host_arrays()
+        A = self.device_arrays() if self.device_built else self.host_arrays()
         items = A["items"][shard_index::max(1, shard_count)]
         leaf = A["leaf"]
         return np.concatenate([np.arange(leaf[i, 0], leaf[i, 0] + leaf[i, 1]) for i in items]) \

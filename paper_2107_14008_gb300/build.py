@@ -20,10 +20,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--ftz=true",
               "--prec-div=true", "--prec-sqrt=true", "--fmad=true", "-Xptxas", "-v",
               "-I" + os.path.join(ROOT, "include")]
+# -ffp-contract=off: the builder's FP64 box tests must round the same way on
+# every host (gcc contracts a*b+c into an FMA by default on aarch64).
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function",
+             "-ffp-contract=off",
              "-I" + os.path.join(ROOT, "include")]
 CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_f64.cu",
-              "p2p_adj.cu", "capi.cu", "noalloc.cu"]
+              "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu"]
 CXX_SOURCES = ["builder.cpp"]
 
 

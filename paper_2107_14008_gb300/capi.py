@@ -23,7 +23,9 @@ PSR_BUILD_NO_FP64 = 1
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
            "psr_check", "psr_table", "psr_autotune",
-           "psr_leaves_host_arrays", "psr_free_leaves", "psr_last_error", "psr_version"]
+           "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
+           "psr_device_build", "psr_device_build_finish", "psr_free_leaves", "psr_last_error",
+           "psr_version"]
 
 
 class psr_box(ctypes.Structure):
@@ -54,6 +56,11 @@ class psr_host_arrays(ctypes.Structure):
                 ("rowptr", ctypes.POINTER(ctypes.c_int64)),
                 ("pairs", ctypes.POINTER(ctypes.c_uint32)),
                 ("items", ctypes.POINTER(ctypes.c_int32))]
+
+
+class psr_regions(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_size_t) for k in
+                ("pf", "pd", "perm", "leaf", "lcen", "rowptr", "pairs", "items", "total")]
 
 
 class PsrError(RuntimeError):
@@ -91,6 +98,12 @@ def lib():
     L.psr_check.argtypes = [vp, vp, ctypes.c_int]
     L.psr_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
     L.psr_leaves_host_arrays.argtypes = [vp, ctypes.POINTER(psr_host_arrays)]
+    L.psr_leaves_regions.argtypes = [vp, ctypes.POINTER(psr_regions)]
+    L.psr_device_build_scratch_bytes.argtypes = [i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.psr_device_build.argtypes = [vp, vp, i64, ctypes.POINTER(psr_box), ctypes.c_int,
+                                   ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_int,
+                                   ctypes.POINTER(vp)]
+    L.psr_device_build_finish.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.psr_free_leaves.argtypes = [vp]
     L.psr_free_leaves.restype = None
     L.psr_last_error.restype = ctypes.c_char_p
@@ -179,6 +192,33 @@ def psr_leaves_host_arrays(h):
     a = psr_host_arrays()
     check(lib().psr_leaves_host_arrays(h, ctypes.byref(a)))
     return a
+
+
+def psr_leaves_regions(h):
+    r = psr_regions()
+    check(lib().psr_leaves_regions(h, ctypes.byref(r)))
+    return r
+
+
+def psr_device_build_scratch_bytes(n):
+    v = ctypes.c_size_t()
+    check(lib().psr_device_build_scratch_bytes(n, ctypes.byref(v)))
+    return v.value
+
+
+def psr_device_build(d_pos, d_mass, n, box, max_leaf, flags, d_scratch, scratch_bytes, stream,
+                     timeout_ms):
+    h = ctypes.c_void_p()
+    check(lib().psr_device_build(ctypes.c_void_p(d_pos), ctypes.c_void_p(d_mass), n,
+                                 ctypes.byref(box), max_leaf, flags, ctypes.c_void_p(d_scratch),
+                                 scratch_bytes, ctypes.c_void_p(stream), timeout_ms,
+                                 ctypes.byref(h)))
+    return h
+
+
+def psr_device_build_finish(h, d_ws, nbytes, stream):
+    return check(lib().psr_device_build_finish(h, ctypes.c_void_p(d_ws), nbytes,
+                                               ctypes.c_void_p(stream)))
 
 
 def psr_free_leaves(h):

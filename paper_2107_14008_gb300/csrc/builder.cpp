@@ -247,6 +247,24 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+BoxDev box_constants(const psr_box& bx)
+{
+    BoxDev d{};
+    d.L = bx.L;
+    d.r_s = bx.r_s;
+    d.r_c = bx.r_c;
+    d.G = bx.G;
+    d.rc2 = bx.r_c * bx.r_c;
+    d.inv_2rs = 1.0 / (2.0 * bx.r_s);
+    d.unit = (float)(std::ldexp(bx.L, -kCentreShift) / (2.0 * bx.r_s));
+    d.x_c = (float)(bx.r_c / (2.0 * bx.r_s));
+    d.x_c2 = d.x_c * d.x_c;
+    d.g_acc = (float)(bx.G / (4.0 * bx.r_s * bx.r_s));
+    d.g_adj = (float)(bx.G / (8.0 * bx.r_s * bx.r_s * bx.r_s));
+    d.g_adjm = (float)(bx.G / (4.0 * bx.r_s * bx.r_s));
+    return d;
+}
+
 Layout make_layout(const Leaves& h)
 {
     Layout L{};
@@ -440,23 +458,7 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
 
         // ---- per-box constants -------------------------------------------
         h->boxdev.resize(nbox);
-        for (int b = 0; b < nbox; ++b) {
-            const psr_box& bx = boxes[b];
-            BoxDev d{};
-            d.L = bx.L;
-            d.r_s = bx.r_s;
-            d.r_c = bx.r_c;
-            d.G = bx.G;
-            d.rc2 = bx.r_c * bx.r_c;
-            d.inv_2rs = 1.0 / (2.0 * bx.r_s);
-            d.unit = (float)(std::ldexp(bx.L, -kCentreShift) / (2.0 * bx.r_s));
-            d.x_c = (float)(bx.r_c / (2.0 * bx.r_s));
-            d.x_c2 = d.x_c * d.x_c;
-            d.g_acc = (float)(bx.G / (4.0 * bx.r_s * bx.r_s));
-            d.g_adj = (float)(bx.G / (8.0 * bx.r_s * bx.r_s * bx.r_s));
-            d.g_adjm = (float)(bx.G / (4.0 * bx.r_s * bx.r_s));
-            h->boxdev[b] = d;
-        }
+        for (int b = 0; b < nbox; ++b) h->boxdev[b] = box_constants(boxes[b]);
 
         // ---- sorted payloads ----------------------------------------------
         h->pf.resize((size_t)ntot * 4);

@@ -268,6 +268,8 @@ int psr_upload(psr_leaves* hh, void* d_ws, size_t bytes, void* stream)
 {
     Leaves* h = reinterpret_cast<Leaves*>(hh);
     if (!h) return fail(PSR_E_ARG, "null handle");
+    if (h->device_built)
+        return fail(PSR_E_STATE, "a device-built handle is written by psr_device_build_finish");
     if (!d_ws || bytes < h->lay.total || (reinterpret_cast<uintptr_t>(d_ws) & 255))
         return fail(PSR_E_WORKSPACE, "workspace must be 256-byte aligned and at least " +
                                          std::to_string(h->lay.total) + " bytes");
@@ -498,6 +500,23 @@ int psr_leaves_host_arrays(const psr_leaves* hh, psr_host_arrays* out)
     out->rowptr = h->rowptr.data();
     out->pairs = h->pairs.data();
     out->items = h->items.data();
+    return PSR_OK;
+}
+
+int psr_leaves_regions(const psr_leaves* hh, psr_regions* out)
+{
+    const Leaves* h = reinterpret_cast<const Leaves*>(hh);
+    if (!h || !out) return fail(PSR_E_ARG, "null argument");
+    const Layout& L = h->lay;
+    out->pf = L.pf;
+    out->pd = L.pd;
+    out->perm = L.perm;
+    out->leaf = L.leaf;
+    out->lcen = L.lcen;
+    out->rowptr = L.rowptr;
+    out->pairs = L.pairs;
+    out->items = L.items;
+    out->total = L.total;
     return PSR_OK;
 }
 

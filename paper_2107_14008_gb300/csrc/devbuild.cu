@@ -1,0 +1,921 @@
+// Device-side leaf and leaf-pair builder: the GPU counterpart of builder.cpp
+// (paper, Section 2: contiguous leaves of at most MAXLEAF particles; Section
+// 3.2: the task list grouped by target leaf, with start and length per leaf).
+// It produces the arrays the host builder produces, bit for bit and in the
+// same order:
+//   1. keys      wrap positions into [0, L), 21-bit quantisation, 63-bit Morton key
+//   2. sort      stable LSD radix sort of (key, index), 8 passes of 8 bits
+//   3. leaves    a particle's leaf is its first ancestor cell, from the root, that
+//                holds at most max_leaf particles; level-21 cells beyond max_leaf
+//                are cut into chunks of max_leaf.  Since that cell contains the
+//                particle and at most max_leaf particles, its extent is found by
+//                binary searches inside a window of +-(max_leaf + 1) sorted keys.
+//   4. tree      a binary radix tree over the leaf cell keys (Karras 2012, equal
+//                keys ordered by leaf index) with bottom-up bounding boxes
+//   5. pairs     per target leaf and periodic image, a depth-first traversal that
+//                keeps every leaf whose box comes closer than r_c.  A node's box
+//                contains its leaves' boxes, so the kept set is exactly the set of
+//                leaves that pass the leaf test, which the host's octree keeps too;
+//                the left-first order visits them in leaf order like the host's
+//                Morton-ordered octree walk.  Counted in one pass, written in a
+//                second after a prefix sum of the counts.
+//   6. schedule  target leaves sorted by evaluated work, largest first (stable)
+// The FP64 tests use the same operations as the host (no contraction).
+//
+// Two calls: psr_device_build runs 1-5 (counting) on the caller's scratch and
+// reads back the sizes; psr_device_build_finish writes the workspace.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <thread>
+
+#include "kcommon.cuh"
+
+namespace psr {
+
+void set_last_error(const std::string& msg);
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per block
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096 values per block
+constexpr int64_t kScanMaxTiles = 65536;              // the top level scans in one block
+constexpr int kStackDepth = 128;                      // tree depth <= 63 key + 27 index bits
+constexpr int kDefaultTimeoutMs = 60000;
+constexpr int64_t kMaxN = (int64_t)1 << 28;           // scan limit: 65536 tiles of 4096
+
+// counters in the scratch (int64 words)
+enum : int {
+    kCntMaxLeaf = 0,
+    kCntPairs = 1,
+    kCntEvaluated = 2,
+    kCntMaxCost = 3,
+    kCntMaxRow = 4,
+    kCntError = 5,  // bit 0 non-finite input, bit 1 stack overflow, bit 2 malformed tree
+    kCntWords = 8,
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch regions (byte offsets); leaf arrays are sized for n leaves (max_leaf 1).
+struct Scratch {
+    size_t wpos, key0, key1, val0, val1, flag, lid, lfirst, llevel, lkey, lbox, lcnt, lcost,
+        tnode, tparl, tpari, tbox, tflag, hist, tiles, total, cnt, bytes;
+};
+
+Scratch scratch_layout(int64_t n)
+{
+    Scratch s{};
+    size_t o = 0;
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    const size_t nb = (N + kSortTile - 1) / kSortTile;
+    const size_t hist = 256 * nb;
+    const size_t big = hist > N + 1 ? hist : N + 1;  // longest scanned array
+    const size_t ntiles = (big + kScanTile - 1) / kScanTile;
+    s.wpos = o;   o = a256(o + 32 * N);  // x, y, z, m (wrapped, FP64)
+    s.key0 = o;   o = a256(o + 8 * N);
+    s.key1 = o;   o = a256(o + 8 * N);
+    s.val0 = o;   o = a256(o + 4 * N);
+    s.val1 = o;   o = a256(o + 4 * N);
+    s.flag = o;   o = a256(o + 8 * N);
+    s.lid = o;    o = a256(o + 8 * N);
+    s.lfirst = o; o = a256(o + 4 * (N + 1));
+    s.llevel = o; o = a256(o + 4 * N);
+    s.lkey = o;   o = a256(o + 8 * N);
+    s.lbox = o;   o = a256(o + 48 * N);
+    s.lcnt = o;   o = a256(o + 8 * N);
+    s.lcost = o;  o = a256(o + 8 * N);
+    s.tnode = o;  o = a256(o + 8 * N);
+    s.tparl = o;  o = a256(o + 4 * N);
+    s.tpari = o;  o = a256(o + 4 * N);
+    s.tbox = o;   o = a256(o + 48 * N);
+    s.tflag = o;  o = a256(o + 4 * N);
+    s.hist = o;   o = a256(o + 8 * hist);
+    s.tiles = o;  o = a256(o + 8 * ntiles);
+    s.total = o;  o = a256(o + 8);
+    s.cnt = o;    o = a256(o + 8 * kCntWords);
+    s.bytes = o;
+    return s;
+}
+
+struct BoxK {
+    double L, scale, unit, inv2rs, rc2m;  // rc2m = r_c^2 (1 + 1e-5), the host's margin
+};
+
+// ------------------------------------------------------------ utilities --
+
+__device__ __forceinline__ uint64_t spread3_d(uint64_t v)
+{
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t compact3_d(uint64_t v)
+{
+    v &= 0x1249249249249249ULL;
+    v = (v | (v >> 2)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v >> 4)) & 0x100f00f00f00f00fULL;
+    v = (v | (v >> 8)) & 0x1f0000ff0000ffULL;
+    v = (v | (v >> 16)) & 0x1f00000000ffffULL;
+    v = (v | (v >> 32)) & 0x1fffffULL;
+    return (uint32_t)v;
+}
+
+// first index in [lo, hi) with a[index] >= x (hi if none)
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t lo,
+                                                   int64_t hi, uint64_t x)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// FP64 gap^2 between box A and box B shifted by sh, in the host builder's
+// order of operations (explicit roundings: no contraction).
+__device__ __forceinline__ double gap2_d(const double* A, const double* B, const double sh[3])
+{
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double l = __dadd_rn(B[a], sh[a]), h = __dadd_rn(B[3 + a], sh[a]);
+        const double g = fmax(0.0, fmax(__dsub_rn(l, A[3 + a]), __dsub_rn(A[a], h)));
+        s = __dadd_rn(s, __dmul_rn(g, g));
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ scan --
+// Exclusive prefix sum of int64 values: tile sums, one block scanning the tile
+// sums, then tile scans with their offsets.  In-place use (in == out) is safe.
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int64_t* in, int64_t m,
+                                                     int64_t* __restrict__ sums)
+{
+    __shared__ int64_t red[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t v = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < m) v += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x == 1024);
+// returns the block total.
+__device__ int64_t block_exclusive(int64_t v, int64_t* ex, int64_t* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t s = sh[lane];
+        int64_t si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, si, o);
+            if (lane >= o) si += t;
+        }
+        sh[lane] = si - s;
+        if (lane == 31) sh[32] = si;
+    }
+    __syncthreads();
+    *ex = inc - v + sh[w];
+    const int64_t total = sh[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t* __restrict__ sums, int64_t nt,
+                                                   int64_t* __restrict__ total)
+{
+    __shared__ int64_t sh[33];
+    const int64_t per = (nt + kScanThreads - 1) / kScanThreads;
+    const int64_t b = (int64_t)threadIdx.x * per, e = b + per < nt ? b + per : nt;
+    int64_t v = 0;
+    for (int64_t k = b; k < e; ++k) v += sums[k];
+    int64_t ex;
+    const int64_t t = block_exclusive(v, &ex, sh);
+    for (int64_t k = b; k < e; ++k) {
+        const int64_t c = sums[k];
+        sums[k] = ex;
+        ex += c;
+    }
+    if (threadIdx.x == 0) *total = t;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const int64_t* in, int64_t m,
+                                                     const int64_t* __restrict__ sums, int64_t* out)
+{
+    __shared__ int64_t sh[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t loc[kScanItems], v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = base + k < m ? in[base + k] : 0;
+        v += loc[k];
+    }
+    int64_t ex;
+    block_exclusive(v, &ex, sh);
+    ex += sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < m) out[base + k] = ex;
+        ex += loc[k];
+    }
+}
+
+int scan_exclusive(const int64_t* in, int64_t* out, int64_t m, int64_t* tiles, int64_t* total,
+                   cudaStream_t st)
+{
+    const int64_t nt = (m + kScanTile - 1) / kScanTile;
+    if (nt > kScanMaxTiles) return (int)cudaErrorInvalidValue;
+    if (nt == 0) return (int)cudaMemsetAsync(total, 0, 8, st);
+    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(in, m, tiles);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(tiles, nt, total);
+    k_scan_apply<<<(unsigned)nt, kScanThreads, 0, st>>>(in, m, tiles, out);
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------ radix sort --
+// Stable LSD radix sort of (64-bit key, int32 value), 8 bits per pass.  Per
+// pass: digit counts per tile (digit-major), their exclusive scan, and a
+// stable scatter: item t of a tile is w*256 + it*32 + lane, ranked warp by
+// warp, iteration by iteration and lane by lane, i.e. in item order.
+
+__device__ __forceinline__ int64_t tile_item(int w, int it, int lane)
+{
+    return (int64_t)w * (kSortItems * 32) + it * 32 + lane;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
+                                                             int64_t n, int shift,
+                                                             int64_t* __restrict__ hist,
+                                                             int64_t nblocks)
+{
+    __shared__ unsigned cnt[256];
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int it = 0; it < kSortItems; ++it) {
+        const int64_t j = base + tile_item(w, it, lane);
+        if (j < n) atomicAdd(&cnt[(keys[j] >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x)
+        hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    int32_t* __restrict__ vout, int64_t n, int shift, const int64_t* __restrict__ off,
+    int64_t nblocks)
+{
+    __shared__ unsigned whist[kSortThreads / 32][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) whist[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    uint64_t key[kSortItems];
+    int32_t val[kSortItems];
+    unsigned rank[kSortItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int64_t j = base + tile_item(w, it, lane);
+        const bool ok = j < n;
+        key[it] = ok ? kin[j] : 0;
+        val[it] = ok ? vin[j] : 0;
+        const unsigned d = ok ? (unsigned)((key[it] >> shift) & 255) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        rank[it] = ok ? whist[w][d] + __popc(peers & lt) : 0u;
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) whist[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {  // exclusive over warps, per digit
+        unsigned s = 0;
+        for (int k = 0; k < kSortThreads / 32; ++k) {
+            const unsigned c = whist[k][d];
+            whist[k][d] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int64_t j = base + tile_item(w, it, lane);
+        if (j < n) {
+            const unsigned d = (unsigned)((key[it] >> shift) & 255);
+            const int64_t pos = off[(int64_t)d * nblocks + blockIdx.x] + whist[w][d] + rank[it];
+            kout[pos] = key[it];
+            vout[pos] = val[it];
+        }
+    }
+}
+
+// Sorts on bits [0, bits) of the keys (bits <= 64); the result ends in (k0, v0).
+int radix_sort(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t* v1, int64_t n, int bits,
+               int64_t* hist, int64_t* tiles, int64_t* total, cudaStream_t st)
+{
+    if (n <= 1) return 0;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    int passes = (bits + 7) / 8;
+    if (passes & 1) ++passes;  // an even count leaves the result in (k0, v0); <= 8
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        uint64_t* ki = (p & 1) ? k1 : k0;
+        int32_t* vi = (p & 1) ? v1 : v0;
+        uint64_t* ko = (p & 1) ? k0 : k1;
+        int32_t* vo = (p & 1) ? v0 : v1;
+        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(ki, n, shift, hist, nb);
+        int e = scan_exclusive(hist, hist, 256 * nb, tiles, total, st);
+        if (e) return e;
+        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nb);
+        if ((e = (int)cudaGetLastError())) return e;
+    }
+    return 0;
+}
+
+// -------------------------------------------------------- keys and leaves --
+
+__global__ void k_keys(const double* __restrict__ pos, const double* __restrict__ mass, int64_t n,
+                       BoxK bx, double* __restrict__ wpos, uint64_t* __restrict__ key,
+                       int32_t* __restrict__ idx, long long* __restrict__ cnt)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t q[3];
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) {
+        double v = pos[3 * i + a];
+        if (!isfinite(v)) {
+            bad = true;
+            v = 0.0;
+        }
+        v = fmod(v, bx.L);
+        if (v < 0) v += bx.L;
+        if (!(v < bx.L)) v = 0.0;
+        wpos[4 * i + a] = v;
+        double qq = floor(__dmul_rn(v, bx.scale));
+        if (qq < 0) qq = 0;
+        if (qq > (double)((1u << kMortonBits) - 1)) qq = (double)((1u << kMortonBits) - 1);
+        q[a] = (uint64_t)qq;
+    }
+    double m = mass ? mass[i] : 1.0 / (double)n;
+    if (!isfinite(m)) {
+        bad = true;
+        m = 0.0;
+    }
+    wpos[4 * i + 3] = m;
+    if (bad) atomicOr((unsigned long long*)(cnt + kCntError), 1ULL);
+    key[i] = (spread3_d(q[0]) << 2) | (spread3_d(q[1]) << 1) | spread3_d(q[2]);
+    idx[i] = (int32_t)i;
+}
+
+__device__ __forceinline__ uint64_t cell_prefix(uint64_t k, int level)
+{
+    const int sh = 3 * (kMortonBits - level);
+    return sh >= 64 ? 0ULL : (k >> sh) << sh;
+}
+
+// [a, b) = the sorted indices of i's level-`level` cell, searched in [lo, hi)
+__device__ __forceinline__ void cell_range(const uint64_t* __restrict__ key, int64_t i, int level,
+                                           int64_t lo, int64_t hi, int64_t& a, int64_t& b)
+{
+    const int sh = 3 * (kMortonBits - level);
+    const uint64_t p = cell_prefix(key[i], level);
+    a = lower_bound_u64(key, lo, i, p);
+    b = sh >= 63 ? hi : lower_bound_u64(key, i + 1, hi, p + (1ULL << sh));
+}
+
+// Leaf level and leaf-start flag of each sorted particle.  In the window
+// [i - max_leaf - 1, i + max_leaf + 2) a cell's clipped count exceeds
+// max_leaf exactly when its full count does, and is exact when it does not.
+__global__ void k_leaf_level(const uint64_t* __restrict__ key, int64_t n, int max_leaf,
+                             int64_t* __restrict__ flag, int32_t* __restrict__ level)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t lo = i - max_leaf - 1 > 0 ? i - max_leaf - 1 : 0;
+    const int64_t hi = i + max_leaf + 2 < n ? i + max_leaf + 2 : n;
+    int64_t a, b;
+    cell_range(key, i, kMortonBits, lo, hi, a, b);
+    bool start;
+    int L;
+    if (b - a > max_leaf) {  // over-full finest cell: chunks of max_leaf from its start
+        L = kMortonBits;
+        const int64_t a0 = lower_bound_u64(key, 0, i, key[i]);
+        start = ((i - a0) % max_leaf) == 0;
+    } else {  // smallest level whose cell holds at most max_leaf (counts fall with level)
+        int l0 = 0, l1 = kMortonBits;
+        while (l0 < l1) {
+            const int mid = (l0 + l1) >> 1;
+            cell_range(key, i, mid, lo, hi, a, b);
+            if (b - a <= max_leaf) l1 = mid;
+            else l0 = mid + 1;
+        }
+        L = l0;
+        cell_range(key, i, L, lo, hi, a, b);
+        start = i == a;
+    }
+    flag[i] = start ? 1 : 0;
+    level[i] = L;
+}
+
+__global__ void k_leaf_fill(const int64_t* __restrict__ flag, const int64_t* __restrict__ lid,
+                            const int32_t* __restrict__ level, const uint64_t* __restrict__ key,
+                            int64_t n, int32_t* __restrict__ lfirst, int32_t* __restrict__ llevel,
+                            uint64_t* __restrict__ lkey)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    const int64_t g = lid[i];
+    lfirst[g] = (int32_t)i;
+    llevel[g] = level[i];
+    lkey[g] = cell_prefix(key[i], level[i]);
+}
+
+__global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64_t n,
+                           const double* __restrict__ wpos, const int32_t* __restrict__ idx,
+                           double* __restrict__ lbox, long long* __restrict__ cnt)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    const int64_t f = lfirst[g], e = g + 1 < nl ? lfirst[g + 1] : n;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t k = f; k < e; ++k) {
+        const int64_t p = idx[k];
+        for (int a = 0; a < 3; ++a) {
+            const double v = wpos[4 * p + a];
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        lbox[6 * g + a] = lo[a];
+        lbox[6 * g + 3 + a] = hi[a];
+    }
+    atomicMax(cnt + kCntMaxLeaf, (long long)(e - f));
+}
+
+// ------------------------------------------------------------------ tree --
+// Internal node i (0 <= i < nl - 1) of the binary radix tree over the sorted
+// leaf cell keys, node 0 the root.  A child code with bit 31 set is a leaf.
+
+constexpr int kLeafBit = (int)0x80000000u;
+
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t nl, int64_t i, int64_t j)
+{
+    if (j < 0 || j >= nl) return -1;
+    const uint64_t a = k[i], b = k[j];
+    if (a == b) return 64 + __clz((unsigned)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+__global__ void k_tree_nodes(const uint64_t* __restrict__ k, int64_t nl, int2* __restrict__ node,
+                             int32_t* __restrict__ parl, int32_t* __restrict__ pari)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nl - 1) return;
+    const int d = delta(k, nl, i, i + 1) > delta(k, nl, i, i - 1) ? 1 : -1;
+    const int dmin = delta(k, nl, i, i - d);
+    int64_t lmax = 2;
+    while (delta(k, nl, i, i + lmax * d) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (delta(k, nl, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(k, nl, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, nl, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int2 c;
+    if (lo == gamma) {
+        c.x = (int)gamma | kLeafBit;
+        parl[gamma] = (int)i;
+    } else {
+        c.x = (int)gamma;
+        pari[gamma] = (int)i;
+    }
+    if (hi == gamma + 1) {
+        c.y = (int)(gamma + 1) | kLeafBit;
+        parl[gamma + 1] = (int)i;
+    } else {
+        c.y = (int)(gamma + 1);
+        pari[gamma + 1] = (int)i;
+    }
+    node[i] = c;
+    if (i == 0) pari[0] = -1;
+}
+
+__device__ __forceinline__ const double* child_box(int c, const double* lbox, const double* tbox)
+{
+    return c < 0 ? lbox + 6 * (int64_t)(c & 0x7fffffff) : tbox + 6 * (int64_t)c;
+}
+
+// Bottom-up boxes: of the two threads that reach a node, the second one
+// (whose sibling subtree is then complete) computes it and moves up.
+__global__ void k_tree_boxes(int64_t nl, const int2* __restrict__ node,
+                             const int32_t* __restrict__ parl, const int32_t* __restrict__ pari,
+                             const double* __restrict__ lbox, double* tbox, int* flags,
+                             long long* cnt)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    int p = parl[g];
+    for (int step = 0; p >= 0; ++step) {
+        if (step > kStackDepth || p >= nl - 1) {
+            atomicOr((unsigned long long*)(cnt + kCntError), 4ULL);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;
+        __threadfence();
+        const int2 c = node[p];
+        const double* A = child_box(c.x, lbox, tbox);
+        const double* B = child_box(c.y, lbox, tbox);
+        for (int a = 0; a < 3; ++a) {
+            tbox[6 * (int64_t)p + a] = fmin(__ldcg(A + a), __ldcg(B + a));
+            tbox[6 * (int64_t)p + 3 + a] = fmax(__ldcg(A + 3 + a), __ldcg(B + 3 + a));
+        }
+        p = pari[p];
+    }
+}
+
+// ----------------------------------------------------------------- pairs --
+// One thread per target leaf.  WRITE = false counts the row and its work;
+// WRITE = true writes the row at rowptr.  Each traversal pops at most
+// 2 nl - 1 nodes; more means a malformed tree, reported, never looped on.
+template <bool WRITE>
+__global__ void k_pairs(int64_t nl, int64_t n, BoxK bx, const int32_t* __restrict__ lfirst,
+                        const double* __restrict__ lbox, const int2* __restrict__ node,
+                        const double* __restrict__ tbox, int64_t* __restrict__ lcnt,
+                        int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
+                        uint32_t* __restrict__ pairs, long long* __restrict__ cnt)
+{
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (I >= nl) return;
+    double A[6];
+    for (int a = 0; a < 6; ++a) A[a] = lbox[6 * I + a];
+    const int64_t nI = (I + 1 < nl ? lfirst[I + 1] : n) - lfirst[I];
+    const int root = nl >= 2 ? 0 : kLeafBit;
+    const double* rbox = child_box(root, lbox, tbox);
+    int stack[kStackDepth];
+    int64_t c = 0, src = 0;
+    int64_t w = WRITE ? rowptr[I] : 0;
+    const int64_t wend = WRITE ? rowptr[I + 1] : 0;
+    for (int code = 0; code < kShiftCodes; ++code) {
+        const double sh[3] = {(code / 9 - 1) * bx.L, ((code / 3) % 3 - 1) * bx.L,
+                              (code % 3 - 1) * bx.L};
+        if (gap2_d(A, rbox, sh) >= bx.rc2m) continue;
+        int sp = 0;
+        stack[sp++] = root;
+        int64_t pops = 0;
+        while (sp > 0) {
+            if (++pops > 2 * nl) {
+                atomicOr((unsigned long long*)(cnt + kCntError), 4ULL);
+                break;
+            }
+            const int nd = stack[--sp];
+            if (gap2_d(A, child_box(nd, lbox, tbox), sh) >= bx.rc2m) continue;
+            if (nd < 0) {
+                const int64_t J = nd & 0x7fffffff;
+                if (WRITE) {
+                    if (w >= wend) {
+                        atomicOr((unsigned long long*)(cnt + kCntError), 4ULL);
+                        break;
+                    }
+                    pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
+                }
+                ++c;
+                src += (J + 1 < nl ? lfirst[J + 1] : n) - lfirst[J];
+            } else {
+                if (sp + 2 > kStackDepth) {
+                    atomicOr((unsigned long long*)(cnt + kCntError), 2ULL);
+                    break;
+                }
+                const int2 ch = node[nd];
+                stack[sp++] = ch.y;  // right first, so the left child pops first
+                stack[sp++] = ch.x;
+            }
+        }
+    }
+    if (!WRITE) {
+        lcnt[I] = c;
+        lcost[I] = src * nI;
+        atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
+        atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
+        atomicMax(cnt + kCntMaxCost, (long long)(src * nI));
+        atomicMax(cnt + kCntMaxRow, (long long)c);
+    }
+}
+
+// --------------------------------------------------------------- payload --
+// The workspace arrays of one leaf: leaf record, integer cell centre (units
+// L / 2^22), leaf-local FP32 coordinates in units of 2 r_s, FP64 copy, perm.
+__global__ void k_payload(const int32_t* __restrict__ lfirst, const int32_t* __restrict__ llevel,
+                          const uint64_t* __restrict__ lkey, int64_t nl, int64_t n, BoxK bx,
+                          const double* __restrict__ wpos, const int32_t* __restrict__ idx,
+                          float4* __restrict__ pf, double4* __restrict__ pd,
+                          int32_t* __restrict__ perm, int4* __restrict__ leaf,
+                          int4* __restrict__ lcen)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    const int64_t f = lfirst[g], e = g + 1 < nl ? lfirst[g + 1] : n;
+    const int L = llevel[g];
+    const uint64_t k = lkey[g];
+    const int sh = kMortonBits - L;
+    const uint32_t sc = 1u << sh;
+    const int32_t cx = (int32_t)((2 * (compact3_d(k >> 2) >> sh) + 1) * sc);
+    const int32_t cy = (int32_t)((2 * (compact3_d(k >> 1) >> sh) + 1) * sc);
+    const int32_t cz = (int32_t)((2 * (compact3_d(k) >> sh) + 1) * sc);
+    leaf[g] = make_int4((int)f, (int)(e - f), 0, 0);
+    lcen[g] = make_int4(cx, cy, cz, L);
+    const double c[3] = {__dmul_rn((double)cx, bx.unit), __dmul_rn((double)cy, bx.unit),
+                         __dmul_rn((double)cz, bx.unit)};
+    for (int64_t q = f; q < e; ++q) {
+        const int64_t p = idx[q];
+        const double x = wpos[4 * p], y = wpos[4 * p + 1], z = wpos[4 * p + 2], m = wpos[4 * p + 3];
+        pf[q] = make_float4((float)__dmul_rn(__dsub_rn(x, c[0]), bx.inv2rs),
+                            (float)__dmul_rn(__dsub_rn(y, c[1]), bx.inv2rs),
+                            (float)__dmul_rn(__dsub_rn(z, c[2]), bx.inv2rs), (float)m);
+        if (pd) pd[q] = make_double4(x, y, z, m);
+        perm[q] = (int32_t)p;
+    }
+}
+
+// schedule keys: maxcost - cost ascending = cost descending; equal costs keep
+// leaf order (stable sort)
+__global__ void k_sched_keys(const int64_t* __restrict__ lcost, int64_t nl, long long maxcost,
+                             uint64_t* __restrict__ key, int32_t* __restrict__ val)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    key[g] = (uint64_t)(maxcost - lcost[g]);
+    val[g] = (int32_t)g;
+}
+
+__global__ void k_copy_total(int64_t* dst, const int64_t* src) { *dst = *src; }
+
+unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int dfail(int code, const std::string& msg)
+{
+    set_last_error(msg);
+    return code;
+}
+
+int dcuda(int e, const char* what)
+{
+    return dfail(PSR_E_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)e));
+}
+
+// Bounded host wait for the stream, then a copy of `bytes` to the host.
+int read_back(void* dst, const void* src, size_t bytes, cudaStream_t st, int timeout_ms)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return dcuda(e, "cudaStreamQuery");
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > timeout_ms) return dfail(PSR_E_TIMEOUT, "device build did not finish within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PSR_OK : dcuda(e, "cudaMemcpyAsync (device build counters)");
+}
+
+BoxK box_k(const psr_box& b)
+{
+    BoxK k;
+    k.L = b.L;
+    k.scale = std::ldexp(1.0, kMortonBits) / b.L;
+    k.unit = std::ldexp(b.L, -kCentreShift);
+    k.inv2rs = 1.0 / (2.0 * b.r_s);
+    k.rc2m = b.r_c * b.r_c * (1.0 + 1e-5);
+    return k;
+}
+
+}  // namespace
+}  // namespace psr
+
+using namespace psr;
+
+extern "C" {
+
+int psr_device_build_scratch_bytes(int64_t n, size_t* bytes)
+{
+    if (!bytes || n < 1 || n > kMaxN)
+        return dfail(PSR_E_ARG, "need 1 <= n <= 2^28 and a non-null output");
+    *bytes = scratch_layout(n).bytes;
+    return PSR_OK;
+}
+
+int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const psr_box* box,
+                     int max_leaf, int flags, void* d_scratch, size_t scratch_bytes, void* stream,
+                     int timeout_ms, psr_leaves** out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!out) return dfail(PSR_E_ARG, "null output");
+    *out = nullptr;
+    if (!d_pos || !box || n < 1 || n > kMaxN)
+        return dfail(PSR_E_ARG, "null argument or n outside [1, 2^28]");
+    if (max_leaf < 1 || max_leaf > kMaxLeaf) return dfail(PSR_E_ARG, "max_leaf must be in [1, 64]");
+    if (!(std::isfinite(box->L) && box->L > 0) || !(std::isfinite(box->r_s) && box->r_s > 0) ||
+        !std::isfinite(box->G))
+        return dfail(PSR_E_ARG, "L, r_s must be finite and positive");
+    if (!(box->r_c > 0) || !(box->r_c < box->L)) return dfail(PSR_E_CUTOFF, "need 0 < r_c < L");
+    const Scratch S = scratch_layout(n);
+    if (!d_scratch || scratch_bytes < S.bytes || (reinterpret_cast<uintptr_t>(d_scratch) & 255))
+        return dfail(PSR_E_WORKSPACE, "scratch must be 256-byte aligned and at least " +
+                                          std::to_string(S.bytes) + " bytes");
+    if (timeout_ms <= 0) timeout_ms = kDefaultTimeoutMs;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* s = static_cast<char*>(d_scratch);
+    double* wpos = (double*)(s + S.wpos);
+    uint64_t* k0 = (uint64_t*)(s + S.key0);
+    uint64_t* k1 = (uint64_t*)(s + S.key1);
+    int32_t* v0 = (int32_t*)(s + S.val0);
+    int32_t* v1 = (int32_t*)(s + S.val1);
+    int64_t* flag = (int64_t*)(s + S.flag);
+    int64_t* lid = (int64_t*)(s + S.lid);
+    int32_t* lfirst = (int32_t*)(s + S.lfirst);
+    int32_t* llevel = (int32_t*)(s + S.llevel);
+    uint64_t* lkey = (uint64_t*)(s + S.lkey);
+    double* lbox = (double*)(s + S.lbox);
+    int64_t* lcnt = (int64_t*)(s + S.lcnt);
+    int64_t* lcost = (int64_t*)(s + S.lcost);
+    int2* tnode = (int2*)(s + S.tnode);
+    int32_t* tparl = (int32_t*)(s + S.tparl);
+    int32_t* tpari = (int32_t*)(s + S.tpari);
+    double* tbox = (double*)(s + S.tbox);
+    int* tflag = (int*)(s + S.tflag);
+    int64_t* hist = (int64_t*)(s + S.hist);
+    int64_t* tiles = (int64_t*)(s + S.tiles);
+    int64_t* total = (int64_t*)(s + S.total);
+    long long* cnt = (long long*)(s + S.cnt);
+    const BoxK bx = box_k(*box);
+
+    int e;
+    if ((e = (int)cudaMemsetAsync(cnt, 0, 8 * kCntWords, st))) return dcuda(e, "cudaMemsetAsync");
+    k_keys<<<nblk(n, 256), 256, 0, st>>>(d_pos, d_mass, n, bx, wpos, k0, v0, cnt);
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "key kernel");
+    if ((e = radix_sort(k0, v0, k1, v1, n, 3 * kMortonBits, hist, tiles, total, st)))
+        return dcuda(e, "radix sort");
+    k_leaf_level<<<nblk(n, 256), 256, 0, st>>>(k0, n, max_leaf, flag, v1);
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "leaf level kernel");
+    if ((e = scan_exclusive(flag, lid, n, tiles, total, st))) return dcuda(e, "scan");
+    k_leaf_fill<<<nblk(n, 256), 256, 0, st>>>(flag, lid, v1, k0, n, lfirst, llevel, lkey);
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "leaf fill kernel");
+    long long c[kCntWords];
+    int64_t nl = 0;
+    if ((e = read_back(&nl, total, 8, st, timeout_ms))) return e;
+    if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
+    if (c[kCntError] & 1) return dfail(PSR_E_ARG, "non-finite position or mass");
+    if (nl < 1 || nl > n || nl >= (1 << 27)) return dfail(PSR_E_ARG, "leaf count out of range");
+    k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, cnt);
+    if (nl >= 2) {
+        if ((e = (int)cudaMemsetAsync(tflag, 0, 4 * (nl - 1), st))) return dcuda(e, "cudaMemsetAsync");
+        k_tree_nodes<<<nblk(nl - 1, 256), 256, 0, st>>>(lkey, nl, tnode, tparl, tpari);
+        k_tree_boxes<<<nblk(nl, 256), 256, 0, st>>>(nl, tnode, tparl, tpari, lbox, tbox, tflag, cnt);
+    }
+    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, tnode, tbox, lcnt, lcost,
+                                                  nullptr, nullptr, cnt);
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "pair count kernel");
+    if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
+    if (c[kCntError] & 2) return dfail(PSR_E_DEVICE, "tree traversal stack overflow");
+    if (c[kCntError] & 4) return dfail(PSR_E_DEVICE, "malformed radix tree");
+    if (c[kCntPairs] >= ((int64_t)1 << 32)) return dfail(PSR_E_ARG, "more than 2^32 leaf pairs");
+
+    Leaves* h = new (std::nothrow) Leaves();
+    if (!h) return dfail(PSR_E_NOMEM, "out of host memory");
+    try {
+        h->nbox = 1;
+        h->boxes.assign(box, box + 1);
+        h->box_first = {0, n};
+        h->n = n;
+        h->max_leaf_req = max_leaf;
+        h->flags = flags;
+        h->n_leaves = nl;
+        h->n_pairs = c[kCntPairs];
+        h->evaluated = c[kCntEvaluated];
+        h->max_leaf = (int)c[kCntMaxLeaf];
+        h->max_row = (int)c[kCntMaxRow];
+        h->has_pd = !(flags & PSR_BUILD_NO_FP64);
+        h->device_built = true;
+        h->boxdev = {box_constants(*box)};
+        h->lay = make_layout(*h);
+    } catch (const std::bad_alloc&) {
+        delete h;
+        return dfail(PSR_E_NOMEM, "out of host memory");
+    }
+    h->db_scratch = s;
+    h->db_maxcost = c[kCntMaxCost];
+    h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = reinterpret_cast<psr_leaves*>(h);
+    return PSR_OK;
+}
+
+int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stream)
+{
+    Leaves* h = reinterpret_cast<Leaves*>(hh);
+    if (!h || !h->db_scratch) return dfail(PSR_E_STATE, "not a pending device build");
+    if (!d_ws || bytes < h->lay.total || (reinterpret_cast<uintptr_t>(d_ws) & 255))
+        return dfail(PSR_E_WORKSPACE, "workspace must be 256-byte aligned and at least " +
+                                          std::to_string(h->lay.total) + " bytes");
+    const int64_t n = h->n, nl = h->n_leaves;
+    const Scratch S = scratch_layout(n);
+    char* s = h->db_scratch;
+    char* w = static_cast<char*>(d_ws);
+    const Layout& L = h->lay;
+    cudaStream_t st = (cudaStream_t)stream;
+    const BoxK bx = box_k(h->boxes[0]);
+    int e, dev = 0, sms = 0;
+    if ((e = (int)cudaGetDevice(&dev))) return dcuda(e, "cudaGetDevice");
+    if ((e = (int)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return dcuda(e, "cudaDeviceGetAttribute");
+    const int32_t* lfirst = (const int32_t*)(s + S.lfirst);
+    k_payload<<<nblk(nl, 128), 128, 0, st>>>(
+        lfirst, (const int32_t*)(s + S.llevel), (const uint64_t*)(s + S.lkey), nl, n, bx,
+        (const double*)(s + S.wpos), (const int32_t*)(s + S.val0), (float4*)(w + L.pf),
+        h->has_pd ? (double4*)(w + L.pd) : nullptr, (int32_t*)(w + L.perm), (int4*)(w + L.leaf),
+        (int4*)(w + L.lcen));
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "payload kernel");
+    // row pointers: exclusive scan of the row lengths, then the total
+    int64_t* rowptr = (int64_t*)(w + L.rowptr);
+    int64_t* tiles = (int64_t*)(s + S.tiles);
+    int64_t* total = (int64_t*)(s + S.total);
+    if ((e = scan_exclusive((const int64_t*)(s + S.lcnt), rowptr, nl, tiles, total, st)))
+        return dcuda(e, "scan");
+    k_copy_total<<<1, 1, 0, st>>>(rowptr + nl, total);
+    k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
+        nl, n, bx, lfirst, (const double*)(s + S.lbox), (const int2*)(s + S.tnode),
+        (const double*)(s + S.tbox), nullptr, nullptr, rowptr, (uint32_t*)(w + L.pairs),
+        (long long*)(s + S.cnt));
+    if ((e = (int)cudaGetLastError())) return dcuda(e, "pair write kernel");
+    // schedule: the particle sort buffers are free again (values in int32
+    // views of the flag / lid regions, both >= 4 nl bytes)
+    uint64_t* k0 = (uint64_t*)(s + S.key0);
+    uint64_t* k1 = (uint64_t*)(s + S.key1);
+    int32_t* v0 = (int32_t*)(s + S.flag);
+    int32_t* v1 = (int32_t*)(s + S.lid);
+    k_sched_keys<<<nblk(nl, 256), 256, 0, st>>>((const int64_t*)(s + S.lcost), nl,
+                                                (long long)h->db_maxcost, k0, v0);
+    int bits = 1;
+    while (bits < 63 && ((uint64_t)h->db_maxcost >> bits)) ++bits;
+    if ((e = radix_sort(k0, v0, k1, v1, nl, bits, (int64_t*)(s + S.hist), tiles, total, st)))
+        return dcuda(e, "schedule sort");
+    if ((e = (int)cudaMemcpyAsync(w + L.items, v0, 4 * nl, cudaMemcpyDeviceToDevice, st)))
+        return dcuda(e, "cudaMemcpyAsync");
+    if ((e = (int)cudaMemcpyAsync(w + L.boxes, h->boxdev.data(), sizeof(BoxDev),
+                                  cudaMemcpyHostToDevice, st)))
+        return dcuda(e, "cudaMemcpyAsync");
+    if ((e = (int)cudaMemsetAsync(w + L.ctrl, 0, kCtrlWords * 4, st))) return dcuda(e, "cudaMemsetAsync");
+    h->d_ws = w;
+    h->ws_bytes = bytes;
+    h->uploaded = true;
+    h->table_key = -1;
+    h->table_xc = -1.0;
+    h->adj_table_key = -1;
+    h->sm_count = sms;
+    h->device = dev;
+    h->db_scratch = nullptr;
+    return PSR_OK;
+}
+
+}  // extern "C"

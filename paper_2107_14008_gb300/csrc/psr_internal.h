@@ -99,6 +99,8 @@ struct Leaves {
     int64_t n_pairs = 0;
     bool has_pd = false;        // FP64 payload present in the workspace
     bool device_built = false;  // arrays were built on the device
+    char* db_scratch = nullptr; // device build between its two calls: the caller's scratch
+    int64_t db_maxcost = 0;     //   and the largest per-leaf cost (schedule sort width)
     // device state
     Layout lay{};
     char* d_ws = nullptr;
@@ -115,6 +117,7 @@ struct Leaves {
 int build_batch(int nbox, const double* const* pos, const double* const* mass, const int64_t* n,
                 const psr_box* boxes, int max_leaf, int flags, Leaves** out, std::string* err);
 Layout make_layout(const Leaves& h);
+BoxDev box_constants(const psr_box& b);  // per-box kernel constants
 
 // kernels (launchers defined in the .cu files; return cudaError_t as int)
 struct FwdArgs {

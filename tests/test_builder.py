@@ -257,7 +257,7 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     structs = {"psr_box": capi.psr_box, "psr_opts": capi.psr_opts, "psr_info": capi.psr_info,
-               "psr_host_arrays": capi.psr_host_arrays}
+               "psr_host_arrays": capi.psr_host_arrays, "psr_regions": capi.psr_regions}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "psr.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
@@ -295,3 +295,48 @@ def test_empty_inputs():
     np.testing.assert_array_equal(A["pf"], B["pf"])
     assert np.all(A["leaf"][:, 2] != 1)  # no leaf belongs to the empty box
     np.testing.assert_array_equal(np.sort(lv.perm), np.arange(lv.n))
+
+
+def test_device_builder_host_side_checks():
+    """Arguments psr_device_build rejects before touching a device, and the
+    scratch size (a linear function of n, about 230 bytes per particle)."""
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_device_build_scratch_bytes(0)
+    assert e.value.code == capi.PSR_E_ARG
+    with pytest.raises(capi.PsrError):
+        capi.psr_device_build_scratch_bytes((1 << 28) + 1)
+    b1, b2 = (capi.psr_device_build_scratch_bytes(n) for n in (1 << 20, 1 << 21))
+    assert 200 * (1 << 20) < b1 < 260 * (1 << 20) and abs(b2 - 2 * b1) < 1 << 16
+    box = capi.psr_box(10.0, 0.5, 2.25, 1.0)
+    fake = 1 << 40  # never dereferenced: every check below fails first
+    for args, code in [((0, 0, 100, box, 32, 0, fake, b1), capi.PSR_E_ARG),
+                       ((fake, 0, 100, box, 0, 0, fake, b1), capi.PSR_E_ARG),
+                       ((fake, 0, 100, box, 65, 0, fake, b1), capi.PSR_E_ARG),
+                       ((fake, 0, 100, capi.psr_box(10.0, 0.5, 10.0, 1.0), 32, 0, fake, b1),
+                        capi.PSR_E_CUTOFF),
+                       ((fake, 0, 100, box, 32, 0, 0, b1), capi.PSR_E_WORKSPACE),
+                       ((fake, 0, 100, box, 32, 0, fake + 8, b1), capi.PSR_E_WORKSPACE),
+                       ((fake, 0, 100, box, 32, 0, fake, 1000), capi.PSR_E_WORKSPACE)]:
+        with pytest.raises(capi.PsrError) as e:
+            capi.psr_device_build(*args, 0, 1000)
+        assert e.value.code == code, args
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_device_build_finish(None, fake, 1 << 20, 0)
+    assert e.value.code == capi.PSR_E_STATE
+
+
+def test_regions_of_a_host_built_handle():
+    """psr_leaves_regions: 256-byte aligned, in layout order, sized for the
+    arrays psr_host_arrays describes."""
+    rng = np.random.default_rng(2)
+    lv = psr.Leaves.build(rng.random((3000, 3)) * 20.0, None, 20.0, 1.5, 6.75)
+    r = capi.psr_leaves_regions(lv._h)
+    inf = lv.info
+    n, nl, npairs = 3000, inf.n_leaves, inf.n_pairs
+    order = [("pf", 16 * n), ("pd", 32 * n), ("perm", 4 * n), ("leaf", 16 * nl),
+             ("lcen", 16 * nl), ("rowptr", 8 * (nl + 1)), ("pairs", 4 * npairs),
+             ("items", 4 * nl)]
+    for (a, size), (b, _) in zip(order, order[1:]):
+        assert getattr(r, a) % 256 == 0
+        assert getattr(r, b) - getattr(r, a) >= size, a
+    assert r.total == inf.device_bytes

@@ -1,0 +1,200 @@
+"""GPU leaf builder (psr_device_build / psr_device_build_finish) against the
+host builder: the workspace it writes must equal, array by array and bit by
+bit, what psr_upload sends for the host-built handle of the same input (the
+host builder is itself checked against the oracle's pair counts and the
+paper's leaf rules in test_builder.py).  Integer and index arrays are
+compared exactly; the FP32/FP64 payloads too, since both builders take the
+same FP64 operations in the same order.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+psr = pytest.importorskip("paper_2107_14008_gb300")
+from paper_2107_14008_gb300 import capi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_14008_gb300 import build
+    build.build()
+
+
+def _box(pos, L, n_pm, mass=None, max_leaf=32):
+    r_s, r_c = synth.box_params(L, n_pm)
+    n = pos.shape[0]
+    m = np.full(n, 1.0 / n) if mass is None else mass
+    return synth.Box(pos=pos, mass=m, L=L, n_pm=n_pm, r_s=r_s, r_c=r_c, max_leaf=max_leaf)
+
+
+def _clustered(n, L=60.0, seed=3, n_pm=16, halos=6):
+    rng = np.random.default_rng(seed)
+    pos, _ = synth.nfw_clustered(n, L, 0.6, halos, rng)
+    return _box(pos, L, n_pm, rng.uniform(0.2, 2.0, n))
+
+
+def _coincident(n_same=1000, n_rest=3000, seed=5):
+    """A pack of identical positions (one finest cell, cut into chunks) in a
+    uniform background."""
+    rng = np.random.default_rng(seed)
+    L = 40.0
+    pos = np.concatenate([np.tile([[11.3, 7.9, 30.2]], (n_same, 1)), rng.random((n_rest, 3)) * L])
+    pos = pos[rng.permutation(pos.shape[0])]
+    return _box(pos, L, 12, rng.uniform(0.5, 1.5, pos.shape[0]), max_leaf=8)
+
+
+def _wrapped(seed=6):
+    """Positions outside [0, L): negative, beyond L, exact multiples of L."""
+    rng = np.random.default_rng(seed)
+    L = 25.0
+    pos = rng.uniform(-3 * L, 4 * L, (4000, 3))
+    pos[:5] = [[0.0, L, -L], [2 * L, 0.5, -0.0], [L - 1e-13, 1e-300, 3.0], [-1e-17, 1, 2],
+               [5 * L, -7 * L, 12.5]]
+    return _box(pos, L, 8)
+
+
+CASES = {
+    "uniform20": lambda: synth.small(nside=20),
+    "clustered": lambda: _clustered(6000),
+    "clustered_leaf1": lambda: _set_leaf(_clustered(3000, seed=7), 1),
+    "clustered_leaf8": lambda: _set_leaf(_clustered(6000, seed=8), 8),
+    "clustered_leaf64": lambda: _set_leaf(_clustered(20000, seed=9), 64),
+    "coincident": _coincident,
+    "wrapped": _wrapped,
+    "nfw64": lambda: synth.adjoint(nside=64),
+    "one": lambda: _box(np.array([[1.0, 2.0, 3.0]]), 10.0, 8),
+    "two": lambda: _box(np.array([[1.0, 2.0, 3.0], [1.5, 2.0, 3.0]]), 10.0, 8),
+    "three_same": lambda: _box(np.array([[4.0, 4.0, 4.0]] * 3), 10.0, 8, max_leaf=1),
+}
+
+
+def _set_leaf(b, max_leaf):
+    b.max_leaf = max_leaf
+    return b
+
+
+def _build_both(b, fp64=True, masses=True):
+    dev = torch.device("cuda")
+    m = b.mass if masses else None
+    host = psr.Leaves.build(b.pos, m, b.L, b.r_s, b.r_c, b.G, b.max_leaf, fp64=fp64)
+    host.upload(dev)
+    pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
+    mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev) if masses else None
+    gpu = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, b.max_leaf, fp64=fp64)
+    return host, gpu
+
+
+def _compare(host, gpu):
+    hi, gi = host.info, gpu.info
+    for k in ("n", "n_leaves", "n_pairs", "n_items", "nbox", "evaluated_pairs", "device_bytes",
+              "max_leaf", "max_row"):
+        assert getattr(gi, k) == getattr(hi, k), k
+    H, D = host.host_arrays(), gpu.device_arrays()
+    for k in ("leaf", "lcen", "rowptr", "pairs", "items"):
+        assert H[k].shape == D[k].shape, k
+        mism = np.flatnonzero(np.any((H[k] != D[k]).reshape(H[k].shape[0], -1), axis=1))
+        assert mism.size == 0, (k, mism[:10])
+    assert np.array_equal(H["pf"].view(np.uint32), D["pf"].view(np.uint32))
+    if H["pd"] is None:
+        assert D["pd"] is None
+    else:
+        assert np.array_equal(H["pd"].view(np.uint64), D["pd"].view(np.uint64))
+    assert np.array_equal(host.perm, D["perm"].astype(np.int64))
+    assert np.array_equal(gpu.perm, host.perm)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_device_build_equals_host_build(case):
+    b = CASES[case]()
+    host, gpu = _build_both(b)
+    _compare(host, gpu)
+
+
+@pytest.mark.parametrize("fp64,masses", [(False, True), (True, False)])
+def test_device_build_flags_and_default_masses(fp64, masses):
+    b = _clustered(5000, seed=11)
+    host, gpu = _build_both(b, fp64=fp64, masses=masses)
+    _compare(host, gpu)
+
+
+def test_device_build_precision_workload():
+    """2.1M clustered particles: many sort tiles, scan tiles and top-level
+    scan entries."""
+    b = synth.precision()
+    host, gpu = _build_both(b)
+    _compare(host, gpu)
+
+
+@pytest.mark.parametrize("precision", [psr.PSR_FP32_TABLE, psr.PSR_FP64])
+def test_forces_from_device_build_are_bitwise_equal(precision):
+    b = _clustered(8000, seed=12)
+    host, gpu = _build_both(b)
+    o = psr.Options(precision=precision)
+    a_h = host.forces(o).cpu().numpy()
+    a_g = gpu.forces(o).cpu().numpy()
+    assert np.array_equal(a_h, a_g)
+    cot = torch.tensor(synth.cotangent(b.n, 3), device="cuda")
+    gh = [t.cpu().numpy() for t in host.adjoint(cot, o)]
+    gg = [t.cpu().numpy() for t in gpu.adjoint(cot, o)]
+    assert np.array_equal(gh[0], gg[0]) and np.array_equal(gh[1], gg[1])
+
+
+def test_device_build_state_and_argument_errors():
+    b = _clustered(2000, seed=13)
+    _, gpu = _build_both(b)
+    with pytest.raises(capi.PsrError) as e:
+        gpu.upload()
+    assert e.value.code == capi.PSR_E_STATE
+    with pytest.raises(capi.PsrError) as e:
+        gpu.host_arrays()
+    assert e.value.code == capi.PSR_E_STATE
+    with pytest.raises(capi.PsrError) as e:  # the build is no longer pending
+        capi.psr_device_build_finish(gpu._h, gpu.workspace.data_ptr(), gpu.workspace.numel(),
+                                     torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == capi.PSR_E_STATE
+    bad = torch.tensor(b.pos, device="cuda")
+    bad[17, 1] = float("nan")
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.device_build(bad, None, b.L, b.r_s, b.r_c)
+    assert e.value.code == capi.PSR_E_ARG
+    badm = torch.ones(b.n, dtype=torch.float64, device="cuda")
+    badm[3] = float("inf")
+    with pytest.raises(capi.PsrError) as e:
+        psr.Leaves.device_build(torch.tensor(b.pos, device="cuda"), badm, b.L, b.r_s, b.r_c)
+    assert e.value.code == capi.PSR_E_ARG
+    # scratch too small
+    n = b.n
+    need = capi.psr_device_build_scratch_bytes(n)
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    pos = torch.tensor(b.pos, device="cuda")
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_device_build(pos.data_ptr(), 0, n, psr._box(b.L, b.r_s, b.r_c), 32, 0,
+                              small.data_ptr(), small.numel(),
+                              torch.cuda.current_stream().cuda_stream, 1000)
+    assert e.value.code == capi.PSR_E_WORKSPACE
+
+
+def test_device_build_on_a_side_stream_and_sharded_launch():
+    b = _clustered(6000, seed=14)
+    host, _ = _build_both(b)
+    s = torch.cuda.Stream()
+    pos = torch.tensor(b.pos, device="cuda")
+    mass = torch.tensor(b.mass, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        gpu = psr.Leaves.device_build(pos, mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf, stream=s)
+        full = gpu.forces(psr.Options(), stream=s)
+        parts = torch.zeros_like(full)
+        for k in range(3):
+            gpu.forces(psr.Options(shard_count=3, shard_index=k), out=parts, stream=s)
+    s.synchronize()
+    assert torch.equal(full, parts)
+    assert np.array_equal(full.cpu().numpy(), host.forces(psr.Options()).cpu().numpy())
+    t0 = gpu.shard_targets(3, 0)
+    assert np.array_equal(t0, host.shard_targets(3, 0))
