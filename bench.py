@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--interp", default="linear", choices=["linear", "cubic"])
     p.add_argument("--accum", default="fp64", choices=["fp64", "kahan"])
     p.add_argument("--fp64-steps", type=int, default=2)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--adjoint-steps", type=int, default=3)
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--no-variants", dest="variants", action="store_false",
@@ -427,27 +427,55 @@ def run_psr(args):
     if args.batch_steps > 0:
         batch = run_batch(args, psr, torch, dev, stream, flush)
 
-    # end to end through the public API, host buffers, copies inside the region
+    # end to end through the public API, host buffers, copies inside the region:
+    # positions and masses from pinned host memory, leaf/pair build on the GPU
+    # (psr_device_build), forward kernel, accelerations back to pinned memory
     e2e = None
     if args.e2e_steps > 0:
-        pos_h = torch.from_numpy(b.pos).pin_memory()
+        pos_h = torch.from_numpy(np.ascontiguousarray(b.pos)).pin_memory()
+        mass_h = torch.from_numpy(np.ascontiguousarray(b.mass)).pin_memory()
         out_h = torch.empty((b.n, 3), dtype=torch.float32).pin_memory()
-        torch.cuda.synchronize()
+        pos_d = torch.empty(pos_h.shape, dtype=torch.float64, device=dev)
+        mass_d = torch.empty(mass_h.shape, dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            pos_d.copy_(pos_h, non_blocking=True)
+            mass_d.copy_(mass_h, non_blocking=True)
+            lv2 = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G,
+                                          max_leaf=b.max_leaf, fp64=False)
+            out_h.copy_(lv2.forces(opts), non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()  # warm-up (allocator, table)
+        same = bool(np.array_equal(out_h.numpy(), acc.cpu().numpy()))
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            lv2 = psr.Leaves.build(pos_h.numpy(), b.mass, b.L, b.r_s, b.r_c, b.G,
-                                   max_leaf=b.max_leaf, fp64=False)
-            lv2.upload(dev)
-            out_h.copy_(lv2.forces(opts))
-            torch.cuda.synchronize()
-            h2d = int(lv2.info.device_bytes)
-            del lv2
+            e2e_step()
         dt = (time.perf_counter() - t0) / args.e2e_steps
+        # the GPU build alone (it ends with a host wait), for the breakdown
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            lv3 = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G,
+                                          max_leaf=b.max_leaf, fp64=False)
+            torch.cuda.synchronize()
+            del lv3
+        build_gpu_ms = (time.perf_counter() - t1) / args.e2e_steps * 1e3
         e2e = {"value": world * evaluated / dt / 1e9, "unit": "G pair-interactions/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": b.n * 3 * 4,
-               "ms_per_step": dt * 1e3,
-               "includes": "host leaf/pair build, workspace upload, forward kernel, "
-                           "acceleration download"}
+               "h2d_bytes_per_step": b.n * 4 * 8, "d2h_bytes_per_step": b.n * 3 * 4,
+               "ms_per_step": dt * 1e3, "device_build_ms": build_gpu_ms,
+               "bitwise_equal_to_device_timed_output": same,
+               "includes": "pinned H2D of positions and masses, GPU leaf/pair build "
+                           "(psr_device_build + finish), forward kernel, D2H of accelerations"}
+        # the same path with the host builder instead, for context
+        t2 = time.perf_counter()
+        lvh = psr.Leaves.build(pos_h.numpy(), mass_h.numpy(), b.L, b.r_s, b.r_c, b.G,
+                               max_leaf=b.max_leaf, fp64=False)
+        lvh.upload(dev)
+        out_h.copy_(lvh.forces(opts))
+        torch.cuda.synchronize()
+        e2e["host_build_path_ms_per_step"] = (time.perf_counter() - t2) * 1e3
+        del lvh
 
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -316,7 +316,7 @@ int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
  * size the workspace from the counts:
  *
  * psr_device_build_scratch_bytes - host: scratch bytes psr_device_build
- * needs for n particles (about 230 per particle).  Errors: PSR_E_ARG
+ * needs for n particles (about 320 per particle).  Errors: PSR_E_ARG
  * (n < 1 or n > 2^28, NULL).
  *
  * psr_device_build - enqueue key, radix sort, leaf, radix tree and pair
@@ -331,8 +331,10 @@ int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
  *   d_scratch device, >= psr_device_build_scratch_bytes(n) bytes, 256-byte
  *             aligned, owned by the caller; it holds the build state until
  *             the work psr_device_build_finish enqueues has run
- * Not capturable in a CUDA graph (it waits on the stream).  Errors:
- * PSR_E_ARG (argument, non-finite position or mass), PSR_E_CUTOFF,
+ * The box must have r_c >= 1e-10 and L <= 1e12 (the walk's FP32 bounds
+ * stay rigorous there).  Not capturable in a CUDA graph (it waits on the
+ * stream).  Errors: PSR_E_ARG (argument, box outside that range, non-finite
+ * position or mass), PSR_E_CUTOFF,
  * PSR_E_WORKSPACE (scratch missing, small or misaligned), PSR_E_CUDA,
  * PSR_E_TIMEOUT, PSR_E_DEVICE (a tree bound check fired: traversal stack
  * overflow or a malformed tree; the build is abandoned), PSR_E_NOMEM.

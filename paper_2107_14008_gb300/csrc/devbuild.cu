@@ -18,9 +18,12 @@
 //                leaves that pass the leaf test, which the host's octree keeps too;
 //                the left-first order visits them in leaf order like the host's
 //                Morton-ordered octree walk.  Counted in one pass, written in a
-//                second after a prefix sum of the counts.
+//                second after a prefix sum of the counts.  The walk prunes with
+//                FP32 bounds (directed rounding) and falls back to the host's FP64
+//                leaf test only where the bounds cannot decide (gap^2 within about
+//                1e-5 of the cutoff): FP64 throughput on this part is 1/64 of FP32.
 //   6. schedule  target leaves sorted by evaluated work, largest first (stable)
-// The FP64 tests use the same operations as the host (no contraction).
+// The FP64 steps use the same operations as the host (no contraction).
 //
 // Two calls: psr_device_build runs 1-5 (counting) on the caller's scratch and
 // reads back the sizes; psr_device_build_finish writes the workspace.
@@ -65,8 +68,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Scratch regions (byte offsets); leaf arrays are sized for n leaves (max_leaf 1).
 struct Scratch {
-    size_t wpos, key0, key1, val0, val1, flag, lid, lfirst, llevel, lkey, lbox, lcnt, lcost,
-        tnode, tparl, tpari, tbox, tflag, hist, tiles, total, cnt, bytes;
+    size_t wpos, key0, key1, val0, val1, flag, lid, lfirst, llevel, lkey, lbox, lrec, lcnt,
+        lcost, tnode, tspan, tparl, tpari, tbox, nodef, tflag, hist, tiles, total, cnt, bytes;
 };
 
 Scratch scratch_layout(int64_t n)
@@ -89,12 +92,15 @@ Scratch scratch_layout(int64_t n)
     s.llevel = o; o = a256(o + 4 * N);
     s.lkey = o;   o = a256(o + 8 * N);
     s.lbox = o;   o = a256(o + 48 * N);
+    s.lrec = o;   o = a256(o + 32 * N);  // FP32 inward leaf box and count
     s.lcnt = o;   o = a256(o + 8 * N);
     s.lcost = o;  o = a256(o + 8 * N);
     s.tnode = o;  o = a256(o + 8 * N);
+    s.tspan = o;  o = a256(o + 8 * N);   // leaf range [lo, hi] of each internal node
     s.tparl = o;  o = a256(o + 4 * N);
     s.tpari = o;  o = a256(o + 4 * N);
     s.tbox = o;   o = a256(o + 48 * N);
+    s.nodef = o;  o = a256(o + 64 * N);  // internal nodes: children and their FP32 boxes
     s.tflag = o;  o = a256(o + 4 * N);
     s.hist = o;   o = a256(o + 8 * hist);
     s.tiles = o;  o = a256(o + 8 * ntiles);
@@ -106,6 +112,7 @@ Scratch scratch_layout(int64_t n)
 
 struct BoxK {
     double L, scale, unit, inv2rs, rc2m;  // rc2m = r_c^2 (1 + 1e-5), the host's margin
+    float thi, tlo;  // FP32 thresholds: thi >= rc2m (1 + 1e-6), tlo <= rc2m (1 - 1e-6)
 };
 
 // ------------------------------------------------------------ utilities --
@@ -456,6 +463,7 @@ __global__ void k_leaf_fill(const int64_t* __restrict__ flag, const int64_t* __r
                             uint64_t* __restrict__ lkey)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == n - 1) lfirst[lid[i] + flag[i]] = (int32_t)n;  // lfirst[nl] = n
     if (i >= n || !flag[i]) return;
     const int64_t g = lid[i];
     lfirst[g] = (int32_t)i;
@@ -465,7 +473,8 @@ __global__ void k_leaf_fill(const int64_t* __restrict__ flag, const int64_t* __r
 
 __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64_t n,
                            const double* __restrict__ wpos, const int32_t* __restrict__ idx,
-                           double* __restrict__ lbox, long long* __restrict__ cnt)
+                           double* __restrict__ lbox, float4* __restrict__ lrec,
+                           long long* __restrict__ cnt)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= nl) return;
@@ -483,6 +492,11 @@ __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64
         lbox[6 * g + a] = lo[a];
         lbox[6 * g + 3 + a] = hi[a];
     }
+    // walk record: the box rounded inward (lo up, hi down) and the count
+    lrec[2 * g] = make_float4(__double2float_ru(lo[0]), __double2float_ru(lo[1]),
+                              __double2float_ru(lo[2]), __int_as_float((int)(e - f)));
+    lrec[2 * g + 1] = make_float4(__double2float_rd(hi[0]), __double2float_rd(hi[1]),
+                                  __double2float_rd(hi[2]), 0.f);
     atomicMax(cnt + kCntMaxLeaf, (long long)(e - f));
 }
 
@@ -501,7 +515,8 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t nl,
 }
 
 __global__ void k_tree_nodes(const uint64_t* __restrict__ k, int64_t nl, int2* __restrict__ node,
-                             int32_t* __restrict__ parl, int32_t* __restrict__ pari)
+                             int2* __restrict__ span, int32_t* __restrict__ parl,
+                             int32_t* __restrict__ pari)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nl - 1) return;
@@ -537,6 +552,7 @@ __global__ void k_tree_nodes(const uint64_t* __restrict__ k, int64_t nl, int2* _
         pari[gamma + 1] = (int)i;
     }
     node[i] = c;
+    span[i] = make_int2((int)lo, (int)hi);
     if (i == 0) pari[0] = -1;
 }
 
@@ -575,64 +591,210 @@ __global__ void k_tree_boxes(int64_t nl, const int2* __restrict__ node,
 }
 
 // ----------------------------------------------------------------- pairs --
+// Internal node i packed for the walk (64 bytes): its children's boxes in
+// FP32 rounded outward (lo down, hi up) and their codes:
+//   q[0] = (l.lo.x, l.lo.y, l.lo.z, l.hi.x)   q[1] = (l.hi.y, l.hi.z, r.lo.x, r.lo.y)
+//   q[2] = (r.lo.z, r.hi.x, r.hi.y, r.hi.z)   q[3] = bits(left, right, lo, hi)
+// where [lo, hi] is the node's leaf range: left covers [lo, gamma], right
+// [gamma + 1, hi], gamma = the left child's index (leaf or internal).
+__global__ void k_tree_pack(int64_t nl, const int2* __restrict__ node,
+                            const int2* __restrict__ span, const double* __restrict__ lbox,
+                            const double* __restrict__ tbox, float4* __restrict__ nodef)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nl - 1) return;
+    const int2 c = node[i];
+    const double* A = child_box(c.x, lbox, tbox);
+    const double* B = child_box(c.y, lbox, tbox);
+    float v[12];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = __double2float_rd(A[a]);
+        v[3 + a] = __double2float_ru(A[3 + a]);
+        v[6 + a] = __double2float_rd(B[a]);
+        v[9 + a] = __double2float_ru(B[3 + a]);
+    }
+    float4* q = nodef + 4 * i;
+    q[0] = make_float4(v[0], v[1], v[2], v[3]);
+    q[1] = make_float4(v[4], v[5], v[6], v[7]);
+    q[2] = make_float4(v[8], v[9], v[10], v[11]);
+    const int2 sp = span[i];
+    q[3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), __int_as_float(sp.x),
+                       __int_as_float(sp.y));
+}
+
+// Bounds on the exact gap^2 between a target box A and a box B shifted by
+// sh, in FP32 with every operation rounded toward the bound (shift given
+// rounded down, sd, and up, su).  Lower bound: boxes rounded outward.
+__device__ __forceinline__ float gap2_lower(const float* alo, const float* ahi, const float* blo,
+                                            const float* bhi, const float* sd, const float* su)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d1 = __fsub_rd(__fadd_rd(blo[a], sd[a]), ahi[a]);
+        const float d2 = __fsub_rd(alo[a], __fadd_ru(bhi[a], su[a]));
+        const float g = fmaxf(0.f, fmaxf(d1, d2));
+        s = __fadd_rd(s, __fmul_rd(g, g));
+    }
+    return s;
+}
+
+// Upper bound: boxes rounded inward (lo up, hi down).
+__device__ __forceinline__ float gap2_upper(const float* alo, const float* ahi, const float* blo,
+                                            const float* bhi, const float* sd, const float* su)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d1 = __fsub_ru(__fadd_ru(blo[a], su[a]), ahi[a]);
+        const float d2 = __fsub_ru(alo[a], __fadd_rd(bhi[a], sd[a]));
+        const float g = fmaxf(0.f, fmaxf(d1, d2));
+        s = __fadd_ru(s, __fmul_ru(g, g));
+    }
+    return s;
+}
+
+// Upper bound on the largest gap^2 between A and any point of box B + sh,
+// which bounds the gap^2 of every leaf inside B: B rounded outward, A
+// rounded inward (alo up, ahi down).
+__device__ __forceinline__ float maxgap2_upper(const float* alo, const float* ahi, const float* blo,
+                                               const float* bhi, const float* sd, const float* su)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e1 = __fsub_ru(__fadd_ru(bhi[a], su[a]), ahi[a]);
+        const float e2 = __fsub_ru(alo[a], __fadd_rd(blo[a], sd[a]));
+        const float g = fmaxf(0.f, fmaxf(e1, e2));
+        s = __fadd_ru(s, __fmul_ru(g, g));
+    }
+    return s;
+}
+
 // One thread per target leaf.  WRITE = false counts the row and its work;
-// WRITE = true writes the row at rowptr.  Each traversal pops at most
-// 2 nl - 1 nodes; more means a malformed tree, reported, never looped on.
+// WRITE = true writes the row at rowptr.  Nodes are pruned when the FP32
+// lower bound of their gap^2 reaches thi (then the host's FP64 test fails
+// for every leaf below); a leaf is kept when the FP32 upper bound is below
+// tlo (then the host's FP64 test passes); only the leaves in between take
+// the host's FP64 test itself.  The walk keeps its current node in a
+// register and stacks a right child only while it descends the left one.
+// Each walk visits at most 2 nl - 1 nodes; more means a malformed tree,
+// reported, never looped on.
 template <bool WRITE>
-__global__ void k_pairs(int64_t nl, int64_t n, BoxK bx, const int32_t* __restrict__ lfirst,
-                        const double* __restrict__ lbox, const int2* __restrict__ node,
-                        const double* __restrict__ tbox, int64_t* __restrict__ lcnt,
-                        int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
-                        uint32_t* __restrict__ pairs, long long* __restrict__ cnt)
+__global__ void __launch_bounds__(128, 8) k_pairs(
+    int64_t nl, int64_t n, BoxK bx, const int32_t* __restrict__ lfirst,
+    const double* __restrict__ lbox, const float4* __restrict__ lrec,
+    const float4* __restrict__ nodef, const double* __restrict__ rootbox,
+    int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
+    uint32_t* __restrict__ pairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
 {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= nl) return;
     double A[6];
-    for (int a = 0; a < 6; ++a) A[a] = lbox[6 * I + a];
-    const int64_t nI = (I + 1 < nl ? lfirst[I + 1] : n) - lfirst[I];
-    const int root = nl >= 2 ? 0 : kLeafBit;
-    const double* rbox = child_box(root, lbox, tbox);
-    int stack[kStackDepth];
+    float aolo[3], aohi[3], ailo[3], aihi[3], rlo[3], rhi[3];
+    for (int a = 0; a < 3; ++a) {
+        A[a] = lbox[6 * I + a];
+        A[3 + a] = lbox[6 * I + 3 + a];
+        aolo[a] = __double2float_rd(A[a]);
+        aohi[a] = __double2float_ru(A[3 + a]);
+        ailo[a] = __double2float_ru(A[a]);
+        aihi[a] = __double2float_rd(A[3 + a]);
+        rlo[a] = __double2float_rd(rootbox[a]);
+        rhi[a] = __double2float_ru(rootbox[3 + a]);
+    }
+    // stack entries: (node code, -1) or a leaf range (first, last) kept whole
+    int2 stack[kStackDepth];
     int64_t c = 0, src = 0;
     int64_t w = WRITE ? rowptr[I] : 0;
     const int64_t wend = WRITE ? rowptr[I + 1] : 0;
-    for (int code = 0; code < kShiftCodes; ++code) {
+    bool bad = false;
+    // keeps leaves [f, l] of this image
+    auto take = [&](int f, int l, int code) {
+        c += l - f + 1;
+        src += lfirst[l + 1] - lfirst[f];
+        if (WRITE) {
+            if (w + (l - f + 1) > wend) {
+                atomicOr(err, 4u);
+                bad = true;
+                return;
+            }
+            for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
+        }
+    };
+    for (int code = 0; code < kShiftCodes && !bad; ++code) {
         const double sh[3] = {(code / 9 - 1) * bx.L, ((code / 3) % 3 - 1) * bx.L,
                               (code % 3 - 1) * bx.L};
-        if (gap2_d(A, rbox, sh) >= bx.rc2m) continue;
+        float sd[3], su[3];
+        for (int a = 0; a < 3; ++a) {
+            sd[a] = __double2float_rd(sh[a]);
+            su[a] = __double2float_ru(sh[a]);
+        }
+        if (gap2_lower(aolo, aohi, rlo, rhi, sd, su) >= bx.thi) continue;
+        if (maxgap2_upper(ailo, aihi, rlo, rhi, sd, su) < bx.tlo) {
+            take(0, (int)nl - 1, code);
+            continue;
+        }
         int sp = 0;
-        stack[sp++] = root;
-        int64_t pops = 0;
-        while (sp > 0) {
-            if (++pops > 2 * nl) {
-                atomicOr((unsigned long long*)(cnt + kCntError), 4ULL);
+        int2 cur = make_int2(nl >= 2 ? 0 : kLeafBit, -1);
+        int64_t visits = 0;
+        for (;;) {
+            if (++visits > 2 * nl) {
+                atomicOr(err, 4u);
+                bad = true;
                 break;
             }
-            const int nd = stack[--sp];
-            if (gap2_d(A, child_box(nd, lbox, tbox), sh) >= bx.rc2m) continue;
-            if (nd < 0) {
-                const int64_t J = nd & 0x7fffffff;
-                if (WRITE) {
-                    if (w >= wend) {
-                        atomicOr((unsigned long long*)(cnt + kCntError), 4ULL);
-                        break;
-                    }
-                    pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
-                }
-                ++c;
-                src += (J + 1 < nl ? lfirst[J + 1] : n) - lfirst[J];
+            int2 next = make_int2(0, -2);  // y == -2: take the next stacked entry
+            if (cur.y >= 0) {  // a whole leaf range deferred behind a left subtree
+                take(cur.x, cur.y, code);
+            } else if (cur.x < 0) {  // a leaf that passed the lower-bound test
+                const int J = cur.x & 0x7fffffff;
+                const float4 r0 = lrec[2 * (int64_t)J], r1 = lrec[2 * (int64_t)J + 1];
+                const float bi_lo[3] = {r0.x, r0.y, r0.z}, bi_hi[3] = {r1.x, r1.y, r1.z};
+                if (gap2_upper(ailo, aihi, bi_lo, bi_hi, sd, su) < bx.tlo ||
+                    gap2_d(A, lbox + 6 * (int64_t)J, sh) < bx.rc2m)
+                    take(J, J, code);
             } else {
-                if (sp + 2 > kStackDepth) {
-                    atomicOr((unsigned long long*)(cnt + kCntError), 2ULL);
-                    break;
+                const float4* q = nodef + 4 * (int64_t)cur.x;
+                const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+                const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
+                const float blo[3] = {q1.z, q1.w, q2.x}, bhi[3] = {q2.y, q2.z, q2.w};
+                const int lc = __float_as_int(q3.x), rc = __float_as_int(q3.y);
+                const int lo = __float_as_int(q3.z), hi = __float_as_int(q3.w);
+                const int gamma = lc & 0x7fffffff;
+                const bool pl = gap2_lower(aolo, aohi, llo, lhi, sd, su) < bx.thi;
+                const bool pr = gap2_lower(aolo, aohi, blo, bhi, sd, su) < bx.thi;
+                const bool fl = pl && maxgap2_upper(ailo, aihi, llo, lhi, sd, su) < bx.tlo;
+                const bool fr = pr && maxgap2_upper(ailo, aihi, blo, bhi, sd, su) < bx.tlo;
+                if (fl) take(lo, gamma, code);
+                if (pl && !fl) {  // the left child needs a visit; the right one waits
+                    if (pr) {
+                        if (sp >= kStackDepth) {
+                            atomicOr(err, 2u);
+                            bad = true;
+                            break;
+                        }
+                        stack[sp++] = fr ? make_int2(gamma + 1, hi) : make_int2(rc, -1);
+                    }
+                    next = make_int2(lc, -1);
+                } else if (fr) {
+                    take(gamma + 1, hi, code);
+                } else if (pr) {
+                    next = make_int2(rc, -1);
                 }
-                const int2 ch = node[nd];
-                stack[sp++] = ch.y;  // right first, so the left child pops first
-                stack[sp++] = ch.x;
+            }
+            if (bad) break;
+            if (next.y != -2) {
+                cur = next;
+            } else if (sp > 0) {
+                cur = stack[--sp];
+            } else {
+                break;
             }
         }
     }
+    if (WRITE && !bad && w != wend) atomicOr(err, 4u);
     if (!WRITE) {
+        const int64_t nI = lfirst[I + 1] - lfirst[I];
         lcnt[I] = c;
         lcost[I] = src * nI;
         atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
@@ -720,6 +882,18 @@ int read_back(void* dst, const void* src, size_t bytes, cudaStream_t st, int tim
     return e == cudaSuccess ? PSR_OK : dcuda(e, "cudaMemcpyAsync (device build counters)");
 }
 
+float float_at_least(double x)
+{
+    float f = (float)x;
+    return (double)f < x ? std::nextafter(f, INFINITY) : f;
+}
+
+float float_at_most(double x)
+{
+    float f = (float)x;
+    return (double)f > x ? std::nextafter(f, -INFINITY) : f;
+}
+
 BoxK box_k(const psr_box& b)
 {
     BoxK k;
@@ -728,6 +902,8 @@ BoxK box_k(const psr_box& b)
     k.unit = std::ldexp(b.L, -kCentreShift);
     k.inv2rs = 1.0 / (2.0 * b.r_s);
     k.rc2m = b.r_c * b.r_c * (1.0 + 1e-5);
+    k.thi = float_at_least(k.rc2m * (1.0 + 1e-6));
+    k.tlo = float_at_most(k.rc2m * (1.0 - 1e-6));
     return k;
 }
 
@@ -760,6 +936,8 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
         !std::isfinite(box->G))
         return dfail(PSR_E_ARG, "L, r_s must be finite and positive");
     if (!(box->r_c > 0) || !(box->r_c < box->L)) return dfail(PSR_E_CUTOFF, "need 0 < r_c < L");
+    if (!(box->r_c >= 1e-10) || !(box->L <= 1e12))
+        return dfail(PSR_E_ARG, "the device builder takes r_c >= 1e-10 and L <= 1e12");
     const Scratch S = scratch_layout(n);
     if (!d_scratch || scratch_bytes < S.bytes || (reinterpret_cast<uintptr_t>(d_scratch) & 255))
         return dfail(PSR_E_WORKSPACE, "scratch must be 256-byte aligned and at least " +
@@ -778,12 +956,15 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
     int32_t* llevel = (int32_t*)(s + S.llevel);
     uint64_t* lkey = (uint64_t*)(s + S.lkey);
     double* lbox = (double*)(s + S.lbox);
+    float4* lrec = (float4*)(s + S.lrec);
     int64_t* lcnt = (int64_t*)(s + S.lcnt);
     int64_t* lcost = (int64_t*)(s + S.lcost);
     int2* tnode = (int2*)(s + S.tnode);
+    int2* tspan = (int2*)(s + S.tspan);
     int32_t* tparl = (int32_t*)(s + S.tparl);
     int32_t* tpari = (int32_t*)(s + S.tpari);
     double* tbox = (double*)(s + S.tbox);
+    float4* nodef = (float4*)(s + S.nodef);
     int* tflag = (int*)(s + S.tflag);
     int64_t* hist = (int64_t*)(s + S.hist);
     int64_t* tiles = (int64_t*)(s + S.tiles);
@@ -808,14 +989,17 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 1) return dfail(PSR_E_ARG, "non-finite position or mass");
     if (nl < 1 || nl > n || nl >= (1 << 27)) return dfail(PSR_E_ARG, "leaf count out of range");
-    k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, cnt);
+    k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, lrec, cnt);
     if (nl >= 2) {
         if ((e = (int)cudaMemsetAsync(tflag, 0, 4 * (nl - 1), st))) return dcuda(e, "cudaMemsetAsync");
-        k_tree_nodes<<<nblk(nl - 1, 256), 256, 0, st>>>(lkey, nl, tnode, tparl, tpari);
+        k_tree_nodes<<<nblk(nl - 1, 256), 256, 0, st>>>(lkey, nl, tnode, tspan, tparl, tpari);
         k_tree_boxes<<<nblk(nl, 256), 256, 0, st>>>(nl, tnode, tparl, tpari, lbox, tbox, tflag, cnt);
+        k_tree_pack<<<nblk(nl - 1, 256), 256, 0, st>>>(nl, tnode, tspan, lbox, tbox, nodef);
     }
-    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, tnode, tbox, lcnt, lcost,
-                                                  nullptr, nullptr, cnt);
+    const double* rootbox = nl >= 2 ? tbox : lbox;
+    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec, nodef, rootbox,
+                                                  lcnt, lcost, nullptr, nullptr, cnt,
+                                                  (unsigned*)(cnt + kCntError));
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair count kernel");
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 2) return dfail(PSR_E_DEVICE, "tree traversal stack overflow");
@@ -869,6 +1053,9 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
     if ((e = (int)cudaGetDevice(&dev))) return dcuda(e, "cudaGetDevice");
     if ((e = (int)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
         return dcuda(e, "cudaDeviceGetAttribute");
+    // the control words first: the pair write kernel reports into the error
+    // word that psr_check reads
+    if ((e = (int)cudaMemsetAsync(w + L.ctrl, 0, kCtrlWords * 4, st))) return dcuda(e, "cudaMemsetAsync");
     const int32_t* lfirst = (const int32_t*)(s + S.lfirst);
     k_payload<<<nblk(nl, 128), 128, 0, st>>>(
         lfirst, (const int32_t*)(s + S.llevel), (const uint64_t*)(s + S.lkey), nl, n, bx,
@@ -883,10 +1070,11 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
     if ((e = scan_exclusive((const int64_t*)(s + S.lcnt), rowptr, nl, tiles, total, st)))
         return dcuda(e, "scan");
     k_copy_total<<<1, 1, 0, st>>>(rowptr + nl, total);
+    const double* lbox = (const double*)(s + S.lbox);
     k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
-        nl, n, bx, lfirst, (const double*)(s + S.lbox), (const int2*)(s + S.tnode),
-        (const double*)(s + S.tbox), nullptr, nullptr, rowptr, (uint32_t*)(w + L.pairs),
-        (long long*)(s + S.cnt));
+        nl, n, bx, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.nodef),
+        nl >= 2 ? (const double*)(s + S.tbox) : lbox, nullptr, nullptr, rowptr,
+        (uint32_t*)(w + L.pairs), nullptr, (unsigned*)(w + L.ctrl) + kCtrlError);
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair write kernel");
     // schedule: the particle sort buffers are free again (values in int32
     // views of the flag / lid regions, both >= 4 nl bytes)
@@ -905,7 +1093,6 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
     if ((e = (int)cudaMemcpyAsync(w + L.boxes, h->boxdev.data(), sizeof(BoxDev),
                                   cudaMemcpyHostToDevice, st)))
         return dcuda(e, "cudaMemcpyAsync");
-    if ((e = (int)cudaMemsetAsync(w + L.ctrl, 0, kCtrlWords * 4, st))) return dcuda(e, "cudaMemsetAsync");
     h->d_ws = w;
     h->ws_bytes = bytes;
     h->uploaded = true;

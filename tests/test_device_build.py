@@ -59,7 +59,19 @@ def _wrapped(seed=6):
     return _box(pos, L, 8)
 
 
+def _lattice_at_cutoff(max_leaf, nside=24):
+    """Unit lattice with r_c^2 (1 + 1e-5) = 9: many leaf-box gaps^2 equal the
+    threshold to rounding, where only the FP64 leaf test can decide."""
+    pos = synth.lattice(nside, float(nside))
+    r_c = 3.0 / np.sqrt(1.0 + 1e-5)
+    n = pos.shape[0]
+    return synth.Box(pos=pos, mass=np.full(n, 1.0 / n), L=float(nside), n_pm=nside,
+                     r_s=r_c / 4.5, r_c=r_c, max_leaf=max_leaf)
+
+
 CASES = {
+    "lattice_cutoff1": lambda: _lattice_at_cutoff(1),
+    "lattice_cutoff8": lambda: _lattice_at_cutoff(8),
     "uniform20": lambda: synth.small(nside=20),
     "clustered": lambda: _clustered(6000),
     "clustered_leaf1": lambda: _set_leaf(_clustered(3000, seed=7), 1),
@@ -91,6 +103,7 @@ def _build_both(b, fp64=True, masses=True):
 
 
 def _compare(host, gpu):
+    gpu.check()  # the pair write kernel reports row mismatches here
     hi, gi = host.info, gpu.info
     for k in ("n", "n_leaves", "n_pairs", "n_items", "nbox", "evaluated_pairs", "device_bytes",
               "max_leaf", "max_row"):
