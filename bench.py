@@ -146,6 +146,9 @@ PRECISION_VARIANTS = [
     ("table cubic 1024", dict(table_n=1024, interp=1)),
     ("table cubic 4096", dict(table_n=4096, interp=1)),
     ("exact erfcf/expf", dict(precision=1)),
+    # the paper's Taylor table (Section 3.3, Eq. int), its node spacing 3/512
+    ("paper Taylor T[2] 384 nodes", dict(table_n=384, interp=2)),
+    ("paper Taylor T[4] 384 nodes", dict(table_n=384, interp=3)),
 ]
 
 

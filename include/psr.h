@@ -63,6 +63,10 @@ extern "C" {
 /* interpolation of the table (PSR_FP32_TABLE) */
 #define PSR_LINEAR 0      /* chord between nodes                            */
 #define PSR_CUBIC 1       /* cubic Hermite on (T_k, T'_k = x_k^2 E_k)       */
+#define PSR_TAYLOR2 2     /* the paper's Taylor table (Section 3.3, Eq. int)
+                             to level T_[2] about the nearest node; forward
+                             only                                           */
+#define PSR_TAYLOR4 3     /* the same to level T_[4]                        */
 /* inner loop of the FP32 forward kernels */
 #define PSR_KERNEL_AUTO 0   /* the library's default (scalar streams)          */
 #define PSR_KERNEL_SCALAR 1 /* one source particle per lane and iteration      */
@@ -81,9 +85,13 @@ typedef struct {
 
 typedef struct {
     int precision;       /* PSR_FP64 | PSR_FP32_EXACT | PSR_FP32_TABLE        */
-    int table_n;         /* table intervals on [0, x_c], power of two in
-                            [64, 8192]; 0 = 1024                              */
-    int interp;          /* PSR_LINEAR | PSR_CUBIC                            */
+    int table_n;         /* table intervals on [0, x_c]: a power of two in
+                            [64, 8192] for PSR_LINEAR / PSR_CUBIC (0 = 1024);
+                            any value in [64, 2048] for the Taylor tables
+                            (0 = 384, the paper's node spacing 3/512 at
+                            x_c = 2.25)                                       */
+    int interp;          /* PSR_LINEAR | PSR_CUBIC | PSR_TAYLOR2 | PSR_TAYLOR4
+                            (the adjoint takes PSR_LINEAR | PSR_CUBIC)        */
     int accum;           /* PSR_ACC_FP64 | PSR_ACC_KAHAN32                    */
     int warps_per_block; /* 1..8; 0 = default (8)                            */
     int blocks_per_sm;   /* 0 = default (occupancy-derived)                   */
@@ -265,7 +273,11 @@ int psr_check(psr_leaves* h, void* cuda_stream, int timeout_ms);
  * table_n + 1 of them; entry table_n is the zero sentinel beyond the
  * cutoff).  Linear: (M_k, D_k, 0, 0) with T = M_k + f D_k, f in
  * [-1/2, 1/2] about the interval midpoint; cubic: (c0, c1, c2, c3) with
- * T = c0 + f (c1 + f (c2 + f c3)).  For tests and inspection.
+ * T = c0 + f (c1 + f (c2 + f c3)).  Taylor (table_n in [64, 2048]): two
+ * float4 per node k = 0..table_n, (c0, c1, c2, c3) and (c4, 0, 0, 0), with
+ * T = c0 + f (c1 + f (c2 + f (c3 + f c4))), f = (x - x_k) table_n / x_c the
+ * offset from the nearest node (c3 = c4 = 0 for PSR_TAYLOR2).  For tests and
+ * inspection.
  */
 int psr_table(int table_n, int interp, double x_c, void* d_out, void* cuda_stream);
 

@@ -14,10 +14,11 @@ import numpy as np
 from . import capi
 from .capi import (PSR_ACC_FP64, PSR_ACC_KAHAN32, PSR_CUBIC, PSR_FP32_EXACT, PSR_FP32_TABLE,
                    PSR_FP64, PSR_KERNEL_AUTO, PSR_KERNEL_PACKED, PSR_KERNEL_SCALAR, PSR_LINEAR,
-                   PsrError)
+                   PSR_TAYLOR2, PSR_TAYLOR4, PsrError)
 
 __all__ = ["Options", "Leaves", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
-           "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_ACC_FP64", "PSR_ACC_KAHAN32",
+           "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_TAYLOR2", "PSR_TAYLOR4",
+           "PSR_ACC_FP64", "PSR_ACC_KAHAN32",
            "PSR_KERNEL_AUTO", "PSR_KERNEL_SCALAR", "PSR_KERNEL_PACKED"]
 
 

@@ -14,7 +14,7 @@ PSR_OK = 0
 PSR_E_ARG, PSR_E_CUTOFF, PSR_E_WORKSPACE, PSR_E_CUDA = -1, -2, -3, -4
 PSR_E_DEVICE, PSR_E_TIMEOUT, PSR_E_NOMEM, PSR_E_STATE = -5, -6, -7, -8
 PSR_FP64, PSR_FP32_EXACT, PSR_FP32_TABLE = 0, 1, 2
-PSR_LINEAR, PSR_CUBIC = 0, 1
+PSR_LINEAR, PSR_CUBIC, PSR_TAYLOR2, PSR_TAYLOR4 = 0, 1, 2, 3
 PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
 PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED = 0, 1, 2
 PSR_BUILD_NO_FP64 = 1

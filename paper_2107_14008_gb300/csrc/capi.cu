@@ -63,11 +63,14 @@ int check_opts(const psr_opts* o, Opts* out)
         return fail(PSR_E_ARG, "psr_opts.kernel out of range");
     if (o->precision < PSR_FP64 || o->precision > PSR_FP32_TABLE)
         return fail(PSR_E_ARG, "psr_opts.precision out of range");
-    int tn = o->table_n ? o->table_n : 1024;
-    if (tn < 64 || tn > kMaxTableN || (tn & (tn - 1)))
-        return fail(PSR_E_ARG, "psr_opts.table_n must be a power of two in [64, 8192]");
-    if (o->interp != PSR_LINEAR && o->interp != PSR_CUBIC)
+    if (o->interp < PSR_LINEAR || o->interp > PSR_TAYLOR4)
         return fail(PSR_E_ARG, "psr_opts.interp out of range");
+    const bool taylor = o->interp == PSR_TAYLOR2 || o->interp == PSR_TAYLOR4;
+    int tn = o->table_n ? o->table_n : (taylor ? kTaylorPaperN : 1024);
+    if (taylor && (tn < 64 || tn > kMaxTaylorN))
+        return fail(PSR_E_ARG, "psr_opts.table_n must be in [64, 2048] for the Taylor tables");
+    if (!taylor && (tn < 64 || tn > kMaxTableN || (tn & (tn - 1))))
+        return fail(PSR_E_ARG, "psr_opts.table_n must be a power of two in [64, 8192]");
     if (o->accum != PSR_ACC_FP64 && o->accum != PSR_ACC_KAHAN32)
         return fail(PSR_E_ARG, "psr_opts.accum out of range");
     int w = o->warps_per_block;
@@ -151,7 +154,7 @@ int ensure_table(Leaves* h, const Opts& o, cudaStream_t st)
 {
     if (o.precision != PSR_FP32_TABLE) return PSR_OK;
     const double x_c = h->boxes[0].r_c / (2.0 * h->boxes[0].r_s);
-    int key = o.table_n * 2 + o.interp;
+    int key = o.table_n * 4 + o.interp;
     if (key == h->table_key && x_c == h->table_xc) return PSR_OK;
     char* t = h->d_ws + h->lay.table;
     int e = launch_table(o.table_n, o.interp, x_c, t, t + (size_t)(kMaxTableN + 1) * 16, st);
@@ -348,6 +351,8 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     Opts o;
     int rc = check_opts(opts, &o);
     if (rc) return rc;
+    if (o.precision == PSR_FP32_TABLE && o.interp != PSR_LINEAR && o.interp != PSR_CUBIC)
+        return fail(PSR_E_ARG, "the adjoint takes PSR_LINEAR or PSR_CUBIC tables");
     if (h->n == 0) return PSR_OK;  // nothing to compute
     if (o.precision == PSR_FP64 && !h->has_pd)
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");
@@ -479,9 +484,11 @@ int psr_check(psr_leaves* hh, void* stream, int timeout_ms)
 int psr_table(int table_n, int interp, double x_c, void* d_out, void* stream)
 {
     if (!d_out) return fail(PSR_E_ARG, "null output");
-    if (table_n < 64 || table_n > kMaxTableN || (table_n & (table_n - 1)))
+    if (interp < PSR_LINEAR || interp > PSR_TAYLOR4) return fail(PSR_E_ARG, "interp out of range");
+    if (interp >= PSR_TAYLOR2 && (table_n < 64 || table_n > kMaxTaylorN))
+        return fail(PSR_E_ARG, "table_n must be in [64, 2048] for the Taylor tables");
+    if (interp < PSR_TAYLOR2 && (table_n < 64 || table_n > kMaxTableN || (table_n & (table_n - 1))))
         return fail(PSR_E_ARG, "table_n must be a power of two in [64, 8192]");
-    if (interp != PSR_LINEAR && interp != PSR_CUBIC) return fail(PSR_E_ARG, "interp out of range");
     if (!(x_c > 0) || !std::isfinite(x_c)) return fail(PSR_E_ARG, "x_c must be positive");
     int e = launch_table(table_n, interp, x_c, d_out, nullptr, stream);
     if (e) return cuda_fail((cudaError_t)e, "table kernel launch");

@@ -33,7 +33,23 @@
 
 namespace psr {
 
-enum { TM_EXACT = 0, TM_LINEAR = 1, TM_CUBIC = 2 };
+enum { TM_EXACT = 0, TM_LINEAR = 1, TM_CUBIC = 2, TM_TAYLOR = 3 };
+
+// Paper's Taylor table (Section 3.3, Eq. int) about the nearest node: entry k
+// is two float4, (c0, c1, c2, c3) and (c4, 0, 0, 0), the expansion about x_k
+// in u - k (table units); nodes k = 0..N all real (x_N = x_c), so the cutoff,
+// inside node N's cell, is an explicit select.
+__device__ __forceinline__ float taylor_T(float u, float nmax, unsigned tab_bias)
+{
+    const float t = fminf(u, nmax);
+    const float fk = t + kMagic;
+    const float f = t - (fk - kMagic);
+    const unsigned ad = (unsigned)__float_as_int(fk) * 32u + tab_bias;
+    const float4 c = lds_f4(ad);
+    const float c4 = lds_f1(ad + 16u);
+    const float v = fmaf(f, fmaf(f, fmaf(f, fmaf(f, c4, c.w), c.z), c.y), c.x);
+    return u < nmax ? v : 0.0f;
+}
 
 // exact T(x) with the hard cutoff
 __device__ __forceinline__ float eval_T_exact(float x, float x_c)
@@ -245,6 +261,8 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
     if (TM == TM_EXACT) {
         return make_float2(eval_T_exact(r2.x * rinv.x * xscale, x_c),
                            eval_T_exact(r2.y * rinv.y * xscale, x_c));
+    } else if (TM == TM_TAYLOR) {  // t = u here (nearest node)
+        return make_float2(taylor_T(t.x, nmax, tab_bias), taylor_T(t.y, nmax, tab_bias));
     } else {
         t.x = fminf(t.x, nmax);
         t.y = fminf(t.y, nmax);
@@ -311,7 +329,8 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
     long long e0 = a.rowptr[I];
     const float eps = kEps2 * sc * sc;
     const float2 eps2 = make_float2(eps, eps);
-    const float2 mhalf = make_float2(-0.5f, -0.5f);
+    // table coordinate: u - 1/2 (interval tables), u (Taylor: nearest node)
+    const float2 mhalf = TM == TM_TAYLOR ? make_float2(0.0f, 0.0f) : make_float2(-0.5f, -0.5f);
     while (e0 < re) {
         int nst;
         e0 += stage_chunk<1>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
@@ -361,6 +380,7 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
                                          float nmax, float x_c, float xscale)
 {
     if (TM == TM_EXACT) return eval_T_exact(r2 * rinv * xscale, x_c);
+    if (TM == TM_TAYLOR) return taylor_T(t, nmax, tab_bias);  // t = u here
     t = fminf(t, nmax);
     const float fk = t + kMagic;
     const float f = t - (fk - kMagic);
@@ -429,8 +449,8 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
                     float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
                     float rinv = rsqrt_ftz(r2);
-                    float Tv = eval_T1<TM>(fmaf(r2, rinv, -0.5f), r2, rinv, tab_bias, nmax, x_c,
-                                           xscale);
+                    float Tv = eval_T1<TM>(fmaf(r2, rinv, TM == TM_TAYLOR ? 0.0f : -0.5f), r2,
+                                           rinv, tab_bias, nmax, x_c, xscale);
                     float w = p.w * Tv * rinv * rinv * rinv;
                     fx[r] = fmaf(w, dx, fx[r]);
                     fy[r] = fmaf(w, dy, fy[r]);
@@ -469,12 +489,17 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const unsigned esize = TM == TM_CUBIC ? 16u : 8u;
+    const unsigned esize = TM == TM_TAYLOR ? 32u : TM == TM_CUBIC ? 16u : 8u;
     const size_t tab_bytes = TM == TM_EXACT ? 0 : (size_t)(a.table_n + 1) * esize;
     float4* stage = reinterpret_cast<float4*>(smem + ((tab_bytes + 15) & ~(size_t)15)) +
                     (size_t)warp * (a.stage_cap + kMetaPerWarp);
     float4* meta = stage + a.stage_cap;
-    if (TM != TM_EXACT) {
+    if (TM == TM_TAYLOR) {
+        const float4* g = reinterpret_cast<const float4*>(a.table);
+        for (int i = threadIdx.x; i < 2 * (a.table_n + 1); i += blockDim.x)
+            reinterpret_cast<float4*>(smem)[i] = g[i];
+        __syncthreads();
+    } else if (TM != TM_EXACT) {
         const float4* g = reinterpret_cast<const float4*>(a.table);
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
             const float4 v = g[i];
@@ -556,6 +581,9 @@ int launch_fwd_f32_variant(const FwdArgs& a, int precision, size_t smem, cudaStr
     if (a.interp == PSR_LINEAR)
         return a.accum == PSR_ACC_FP64 ? launch_c<TM_LINEAR, PSR_ACC_FP64, PK>(a, smem, st)
                                        : launch_c<TM_LINEAR, PSR_ACC_KAHAN32, PK>(a, smem, st);
+    if (a.interp == PSR_TAYLOR2 || a.interp == PSR_TAYLOR4)
+        return a.accum == PSR_ACC_FP64 ? launch_c<TM_TAYLOR, PSR_ACC_FP64, PK>(a, smem, st)
+                                       : launch_c<TM_TAYLOR, PSR_ACC_KAHAN32, PK>(a, smem, st);
     return a.accum == PSR_ACC_FP64 ? launch_c<TM_CUBIC, PSR_ACC_FP64, PK>(a, smem, st)
                                    : launch_c<TM_CUBIC, PSR_ACC_KAHAN32, PK>(a, smem, st);
 }
@@ -569,6 +597,8 @@ const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_lea
         return accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
     if (interp == PSR_LINEAR)
         return accum == PSR_ACC_FP64 ? PSR_PICK(TM_LINEAR, PSR_ACC_FP64) : PSR_PICK(TM_LINEAR, PSR_ACC_KAHAN32);
+    if (interp == PSR_TAYLOR2 || interp == PSR_TAYLOR4)
+        return accum == PSR_ACC_FP64 ? PSR_PICK(TM_TAYLOR, PSR_ACC_FP64) : PSR_PICK(TM_TAYLOR, PSR_ACC_KAHAN32);
     return accum == PSR_ACC_FP64 ? PSR_PICK(TM_CUBIC, PSR_ACC_FP64) : PSR_PICK(TM_CUBIC, PSR_ACC_KAHAN32);
 #undef PSR_PICK
 }

@@ -72,6 +72,12 @@ __device__ __forceinline__ unsigned smem_u32(const void* p)
 }
 
 // Loads from read-only shared data (the interpolation table): no ordering.
+__device__ __forceinline__ float lds_f1(unsigned a)
+{
+    float v;
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ float2 lds_f2(unsigned a)
 {
     float2 v;

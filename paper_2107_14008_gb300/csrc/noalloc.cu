@@ -85,9 +85,12 @@ extern "C" int psr_p2p_forces_noalloc(psr_leaves* hh, const psr_opts* opts, void
     int precision = 0;
     int rc = prepare_forward(h, opts, &a, &precision);
     if (rc) return rc;
-    if (precision == PSR_FP32_TABLE && a.table_n > kNoAllocMaxTableN) {
-        set_last_error("psr_p2p_forces_noalloc: table_n " + std::to_string(a.table_n) +
-                       " exceeds the 4096 intervals its fixed scratch array holds");
+    if (precision == PSR_FP32_TABLE &&
+        (size_t)(a.table_n + 1) * (a.interp == PSR_LINEAR || a.interp == PSR_CUBIC ? 16 : 32) >
+            kTableBytes) {
+        set_last_error("psr_p2p_forces_noalloc: a table of " + std::to_string(a.table_n) +
+                       " intervals exceeds its fixed scratch array (4096 intervals; every "
+                       "Taylor table fits)");
         return PSR_E_ARG;
     }
     void* scratch = nullptr;

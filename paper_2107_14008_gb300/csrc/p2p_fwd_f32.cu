@@ -15,11 +15,29 @@ const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_lea
 // Entries k = 0..N-1 describe [x_k, x_{k+1}], x_k = k x_c / N, as functions of
 // f = (x - x_k)/h - 1/2 in [-1/2, 1/2]; entry N is zero (beyond the cutoff).
 // Second half (offset N+1): the same for Q(x) = exp(-x^2), used by the adjoint.
+// Taylor modes (Eq. int of Section 3.3): node k = 0..N, two float4 per node,
+// the level-2 or level-4 expansion about x_k in powers of f = (x - x_k)/h:
+//   T_k + x_k^2 E_k eps - x_k (x_k^2 - 1) E_k eps^2
+//       + (2/3 x_k^4 - 5/3 x_k^2 + 1/3) E_k eps^3 - x_k (x_k^4/3 - 3/2 x_k^2 + 1) E_k eps^4,
+// eps = f h, E_k = -4 exp(-x_k^2) / sqrt(pi), T_k = erfc(x_k) - x_k E_k / 2.
 __global__ void table_kernel(int N, int interp, double x_c, float4* __restrict__ tT,
                              float4* __restrict__ tQ)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > N) return;
+    if (interp == PSR_TAYLOR2 || interp == PSR_TAYLOR4) {
+        const double h = x_c / N, x = k * h, x2 = x * x;
+        const double E = -2.0 * 1.1283791670955126 * exp(-x2);
+        const double c0 = erfc(x) - 0.5 * x * E;
+        const double c1 = x2 * E * h;
+        const double c2 = -x * (x2 - 1.0) * E * h * h;
+        const bool four = interp == PSR_TAYLOR4;
+        const double c3 = four ? (2.0 / 3.0 * x2 * x2 - 5.0 / 3.0 * x2 + 1.0 / 3.0) * E * h * h * h : 0.0;
+        const double c4 = four ? -x * (x2 * x2 / 3.0 - 1.5 * x2 + 1.0) * E * h * h * h * h : 0.0;
+        tT[2 * k] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
+        tT[2 * k + 1] = make_float4((float)c4, 0.f, 0.f, 0.f);
+        return;
+    }
     if (k == N) {
         tT[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tQ) tQ[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -54,13 +72,18 @@ int launch_table(int table_n, int interp, double x_c, void* d_out, void* d_q_out
     return (int)cudaGetLastError();
 }
 
+// bytes of one table entry in shared memory (and in global for Taylor)
+size_t table_entry_bytes(int interp)
+{
+    return interp == PSR_LINEAR ? 8 : interp == PSR_CUBIC ? 16 : 32;
+}
+
 // ---------------------------------------------------------------- launch --
 constexpr int kMetaPerWarpHost = 32;
 
 size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 {
-    size_t tab = precision != PSR_FP32_TABLE ? 0
-               : (size_t)(table_n + 1) * (interp == PSR_LINEAR ? 8 : 16);
+    size_t tab = precision != PSR_FP32_TABLE ? 0 : (size_t)(table_n + 1) * table_entry_bytes(interp);
     return ((tab + 15) & ~(size_t)15) + (size_t)warps * (cap + kMetaPerWarpHost) * 16;
 }
 

@@ -21,6 +21,8 @@ constexpr int kCentreShift = 22;
 constexpr int kMaxLeaf = 64;
 constexpr int kShiftCodes = 27;  // (nx+1)*9 + (ny+1)*3 + (nz+1)
 constexpr int kMaxTableN = 8192;
+constexpr int kMaxTaylorN = 2048;    // Taylor tables: 32-byte entries
+constexpr int kTaylorPaperN = 384;   // x_c / 384 = 3 / 512 at x_c = 2.25, the paper's spacing
 
 // Per-box constants as the kernels see them (plain old data, 16B aligned).
 struct alignas(16) BoxDev {
@@ -117,6 +119,7 @@ struct Leaves {
 int build_batch(int nbox, const double* const* pos, const double* const* mass, const int64_t* n,
                 const psr_box* boxes, int max_leaf, int flags, Leaves** out, std::string* err);
 Layout make_layout(const Leaves& h);
+size_t table_entry_bytes(int interp);  // p2p_fwd_f32.cu
 BoxDev box_constants(const psr_box& b);  // per-box kernel constants
 
 // kernels (launchers defined in the .cu files; return cudaError_t as int)

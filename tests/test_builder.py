@@ -342,3 +342,19 @@ def test_regions_of_a_host_built_handle():
         assert getattr(r, a) % 256 == 0
         assert getattr(r, b) - getattr(r, a) >= size, a
     assert r.total == inf.device_bytes
+
+
+def test_table_argument_checks():
+    """psr_table validates its arguments before any device work: power-of-two
+    interval counts for the interval tables, [64, 2048] for the Taylor
+    tables (Section 3.3, Eq. int)."""
+    fake = 1 << 40  # never written: every call below fails its checks first
+    for n, interp in [(384, capi.PSR_LINEAR), (384, capi.PSR_CUBIC), (32, capi.PSR_LINEAR),
+                      (16384, capi.PSR_CUBIC), (4096, capi.PSR_TAYLOR2), (63, capi.PSR_TAYLOR4),
+                      (1024, 4), (1024, -1)]:
+        with pytest.raises(capi.PsrError) as e:
+            capi.psr_table(n, interp, 2.25, fake, 0)
+        assert e.value.code == capi.PSR_E_ARG, (n, interp)
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_table(384, capi.PSR_TAYLOR2, -1.0, fake, 0)
+    assert e.value.code == capi.PSR_E_ARG

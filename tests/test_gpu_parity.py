@@ -59,11 +59,11 @@ CASES = {
 _oracle_cache = {}
 
 
-def oracle_acc(b, key, t_mode=oracle.T_EXACT, table_n=1024):
-    k = (key, t_mode, table_n)
+def oracle_acc(b, key, t_mode=oracle.T_EXACT, table_n=1024, level=4):
+    k = (key, t_mode, table_n, level)
     if k not in _oracle_cache:
         _oracle_cache[k] = oracle.forces(b.pos % b.L, b.mass, b.L, b.r_s, b.r_c, b.G,
-                                         t_mode=t_mode, table_n=table_n, cells=True)
+                                         t_mode=t_mode, table_n=table_n, level=level, cells=True)
     return _oracle_cache[k]
 
 
@@ -449,3 +449,77 @@ def test_empty_handle_and_empty_box_in_a_batch():
     a2, _ = gpu_forces(b2, psr.Options())
     np.testing.assert_array_equal(acc[:b1.n], a1.astype(np.float32))
     np.testing.assert_array_equal(acc[b1.n:], a2.astype(np.float32))
+
+
+# ---- the paper's Taylor table (Section 3.3, Eq. int), forward only -------
+
+TAYLOR = [(psr.PSR_TAYLOR2, 2), (psr.PSR_TAYLOR4, 4)]
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "small_box"])
+@pytest.mark.parametrize("interp,level", TAYLOR)
+@pytest.mark.parametrize("table_n", [384, 1000])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_taylor_table_matches_interpolated_oracle(case, interp, level, table_n, kernel):
+    """Same nodes, level and nearest-node rule as the oracle's Taylor mode: what
+    remains is FP32 rounding (table_n 384 is the paper's spacing 3/512)."""
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case, oracle.T_TAYLOR, table_n, level)
+    acc, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP32_TABLE, table_n=table_n,
+                                       interp=interp, kernel=kernel), 32)
+    assert rel_rms(acc, ref) < 2e-6
+    exact, _, _ = oracle_acc(b, case)
+    assert rel_rms(acc, exact) < 2e-5
+
+
+@pytest.mark.parametrize("interp,level", TAYLOR)
+@pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
+def test_taylor_table_wide_leaves_and_counts(interp, level, accum):
+    b = CASES["clustered"]()
+    ref, pairs, _ = oracle_acc(b, "clustered", oracle.T_TAYLOR, 384, level)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=64).upload()
+    o = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=384, interp=interp, accum=accum)
+    acc = lv.forces(o).double().cpu().numpy()
+    assert rel_rms(acc, ref) < 2e-6
+    lv.forces(psr.Options(precision=o.precision, table_n=384, interp=interp, count_pairs=True))
+    assert abs(lv.pair_count() - int(pairs.sum())) <= max(2, int(1e-6 * pairs.sum()))
+    lv.check()
+
+
+@pytest.mark.parametrize("interp,level", TAYLOR)
+@pytest.mark.parametrize("table_n", [64, 384, 2048])
+def test_taylor_table_values(interp, level, table_n):
+    x_c = 2.25
+    out = torch.zeros((2 * (table_n + 1), 4), dtype=torch.float32, device="cuda")
+    capi.psr_table(table_n, interp, x_c, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    tab = out.double().cpu().numpy().reshape(table_n + 1, 8)
+    if level == 2:
+        assert np.all(tab[:, 3:5] == 0.0)
+    h = x_c / table_n
+    x = np.linspace(0, x_c * (1 - 1e-9), 20011)
+    k = np.rint(x / h).astype(int)
+    f = x / h - k
+    c = tab[k]
+    val = c[:, 0] + f * (c[:, 1] + f * (c[:, 2] + f * (c[:, 3] + f * c[:, 4])))
+    ref = oracle.T(x, oracle.T_TAYLOR, table_n, x_c, level)
+    assert np.max(np.abs(val - ref)) < 4e-7  # FP32 rounding of the coefficients
+
+
+def test_taylor_table_is_forward_only_and_runs_without_allocation():
+    b = CASES["small_box"]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
+    o = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=384, interp=psr.PSR_TAYLOR2)
+    with pytest.raises(capi.PsrError) as e:
+        lv.adjoint(torch.zeros((b.n, 3), device="cuda"), o)
+    assert e.value.code == capi.PSR_E_ARG
+    a1 = lv.forces(o)
+    a2 = torch.empty_like(a1)
+    capi.psr_p2p_forces_noalloc(lv._h, o.c(), a2.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert torch.equal(a1, a2)
+    big = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=2048, interp=psr.PSR_TAYLOR4)
+    a3 = lv.forces(big)
+    capi.psr_p2p_forces_noalloc(lv._h, big.c(), a2.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    assert torch.equal(a3, a2)
+    lv.check()
