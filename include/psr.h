@@ -271,8 +271,10 @@ int psr_check(psr_leaves* h, void* cuda_stream, int timeout_ms);
  * psr_table - device: write the interpolation table the FP32 table path
  * uses for (table_n, interp) over [0, x_c] into d_out (float4 entries,
  * table_n + 1 of them; entry table_n is the zero sentinel beyond the
- * cutoff).  Linear: (M_k, D_k, 0, 0) with T = M_k + f D_k, f in
- * [-1/2, 1/2] about the interval midpoint; cubic: (c0, c1, c2, c3) with
+ * cutoff).  Linear: (M_k, D_k, A_k, 0) with T = M_k + f D_k, f in
+ * [-1/2, 1/2] about the interval midpoint, equivalently T = A_k + (k + f) D_k
+ * (A_k = M_k - k D_k, the form the forward kernel evaluates); cubic:
+ * (c0, c1, c2, c3) with
  * T = c0 + f (c1 + f (c2 + f c3)).  Taylor (table_n in [64, 2048]): two
  * float4 per node k = 0..table_n, (c0, c1, c2, c3) and (c4, 0, 0, 0), with
  * T = c0 + f (c1 + f (c2 + f (c3 + f c4))), f = (x - x_k) table_n / x_c the

@@ -270,9 +270,9 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
         const float2 kf = add2(fk, make_float2(-kMagic, -kMagic));
         const float2 f = fma2(kf, make_float2(-1.0f, -1.0f), t);
         const unsigned ka = (unsigned)__float_as_int(fk.x), kb = (unsigned)__float_as_int(fk.y);
-        if (TM == TM_LINEAR) {
+        if (TM == TM_LINEAR) {  // (A_k, D_k): T = A_k + t D_k
             const float2 ca = lds_f2(ka * 8u + tab_bias), cb = lds_f2(kb * 8u + tab_bias);
-            return make_float2(fmaf(f.x, ca.y, ca.x), fmaf(f.y, cb.y, cb.x));
+            return fma2(t, make_float2(ca.y, cb.y), make_float2(ca.x, cb.x));
         } else {
             const float4 ca = lds_f4(ka * 16u + tab_bias), cb = lds_f4(kb * 16u + tab_bias);
             return make_float2(fmaf(f.x, fmaf(f.x, fmaf(f.x, ca.w, ca.z), ca.y), ca.x),
@@ -383,12 +383,12 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
     if (TM == TM_TAYLOR) return taylor_T(t, nmax, tab_bias);  // t = u here
     t = fminf(t, nmax);
     const float fk = t + kMagic;
-    const float f = t - (fk - kMagic);
     const unsigned k = (unsigned)__float_as_int(fk);
-    if (TM == TM_LINEAR) {
+    if (TM == TM_LINEAR) {  // (A_k, D_k): T = A_k + t D_k, no offset f needed
         const float2 c = lds_f2(k * 8u + tab_bias);
-        return fmaf(f, c.y, c.x);
+        return fmaf(t, c.y, c.x);
     } else {
+        const float f = t - (fk - kMagic);
         const float4 c = lds_f4(k * 16u + tab_bias);
         return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
     }
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
             const float4 v = g[i];
             if (TM == TM_LINEAR)
-                reinterpret_cast<float2*>(smem)[i] = make_float2(v.x, v.y);
+                reinterpret_cast<float2*>(smem)[i] = make_float2(v.z, v.y);  // (A_k, D_k)
             else
                 reinterpret_cast<float4*>(smem)[i] = v;
         }

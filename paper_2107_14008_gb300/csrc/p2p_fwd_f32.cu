@@ -14,6 +14,9 @@ const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_lea
 // ------------------------------------------------------------------ table --
 // Entries k = 0..N-1 describe [x_k, x_{k+1}], x_k = k x_c / N, as functions of
 // f = (x - x_k)/h - 1/2 in [-1/2, 1/2]; entry N is zero (beyond the cutoff).
+// Linear entries are (M_k, D_k, A_k, 0): the chord is M_k + f D_k, or, with
+// t = u - 1/2 = k + f (u = x/h), A_k + t D_k where A_k = M_k - k D_k, which
+// the forward kernel evaluates in one FMA without forming f.
 // Second half (offset N+1): the same for Q(x) = exp(-x^2), used by the adjoint.
 // Taylor modes (Eq. int of Section 3.3): node k = 0..N, two float4 per node,
 // the level-2 or level-4 expansion about x_k in powers of f = (x - x_k)/h:
@@ -52,7 +55,10 @@ __global__ void table_kernel(int N, int interp, double x_c, float4* __restrict__
     double D0 = -2.0 * c2 * x0 * x0 * q0, D1 = -2.0 * c2 * x1 * x1 * q1;
     double P0 = -2.0 * x0 * q0, P1 = -2.0 * x1 * q1;
     auto make = [&](double f0, double f1, double d0, double d1) {
-        if (interp == PSR_LINEAR) return make_float4((float)(0.5 * (f0 + f1)), (float)(f1 - f0), 0.f, 0.f);
+        if (interp == PSR_LINEAR) {
+            const double m = 0.5 * (f0 + f1), d = f1 - f0;
+            return make_float4((float)m, (float)d, (float)(m - k * d), 0.f);
+        }
         // Hermite cubic in s = f + 1/2: a0 + a1 s + a2 s^2 + a3 s^3
         double a0 = f0, a1 = h * d0;
         double a2 = -3.0 * f0 - 2.0 * h * d0 + 3.0 * f1 - h * d1;

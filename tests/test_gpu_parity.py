@@ -162,6 +162,11 @@ def test_table_kernel_values(interp, mode, table_n):
     c = tab[k]
     if interp == psr.PSR_LINEAR:
         val = c[:, 0] + f * c[:, 1]
+        # the intercept form the forward kernel evaluates: A_k + (k + f) D_k
+        val2 = c[:, 2] + (k + f) * c[:, 1]
+        ref2 = oracle.T(x, mode, table_n, x_c)
+        assert np.max(np.abs(val2 - ref2)) < 4e-7 + 2.0 ** -24 * np.max(np.abs(k * c[:, 1]))
+        assert np.all(tab[table_n] == 0.0)
     else:
         val = c[:, 0] + f * (c[:, 1] + f * (c[:, 2] + f * c[:, 3]))
     ref = oracle.T(x, mode, table_n, x_c)
