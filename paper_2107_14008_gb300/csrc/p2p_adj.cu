@@ -34,13 +34,13 @@ __device__ __forceinline__ void eval_TQ(float t, float x, float x_c, unsigned ta
     } else {
         t = fminf(t, nmax);
         const float fk = t + kMagic;
-        const float f = t - (fk - kMagic);
         const unsigned a = (unsigned)__float_as_int(fk) * 16u + tab_bias;
         const float4 c = lds_f4(a);
-        if (TM == TM_LINEAR) {
-            T = fmaf(f, c.y, c.x);
-            Q = fmaf(f, c.w, c.z);
+        if (TM == TM_LINEAR) {  // (A_T, D_T, A_Q, D_Q): intercept form, no offset f
+            T = fmaf(t, c.y, c.x);
+            Q = fmaf(t, c.w, c.z);
         } else {
+            const float f = t - (fk - kMagic);
             const float4 d = lds_f4(a + q_off);
             T = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
             Q = fmaf(f, fmaf(f, fmaf(f, d.w, d.z), d.y), d.x);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
             if (TM == TM_LINEAR) {
                 const float4 u = g[i], v = gq[i];
-                sT[i] = make_float4(u.x, u.y, v.x, v.y);
+                sT[i] = make_float4(u.z, u.y, v.z, v.y);  // (A_T, D_T, A_Q, D_Q)
             } else {
                 sT[i] = g[i];
                 sT[a.table_n + 1 + i] = gq[i];
