@@ -367,6 +367,50 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
                      void* cuda_stream, int timeout_ms, psr_leaves** out);
 int psr_device_build_finish(psr_leaves* h, void* d_ws, size_t bytes, void* cuda_stream);
 
+/* ------------------------------------------------- long-range PM part */
+/*
+ * The long-range part of the PM-FMM split (paper, Section 2): phi_long solves
+ * Poisson's equation on an N_PM^3 mesh with the Gaussian-filtered Green's
+ * function -4 pi G exp(-k^2 r_s^2) / k^2 (the Fourier complement of the
+ * short-range erfc(r / 2 r_s) of Eq. tr; the paper prints exp(-k^2/4r_s^2),
+ * which is not its complement), k = 0 dropped.  Cloud-in-cell (CIC) mass
+ * assignment onto mesh points g L / N_PM, FFT (cuFFT), division by the
+ * squared CIC window unless PSR_PM_NO_DECONVOLVE, spectral gradient -i k
+ * (Nyquist planes zeroed), inverse FFT per axis, CIC interpolation back.
+ * psr_p2p_forces + psr_pm_forces (PSR_PM_ACCUMULATE) is the total periodic
+ * acceleration of the split, short range truncated at r_c.
+ *
+ * psr_pm_create - host: cuFFT plans for an n_pm^3 mesh (n_pm even, in
+ *   [8, 1024]); cuFFT may allocate plan data here, never the FFT work area.
+ *   Errors: PSR_E_ARG, PSR_E_NOMEM, PSR_E_CUDA.
+ * psr_pm_scratch_bytes - host: scratch psr_pm_forces needs (about 28 n_pm^3
+ *   bytes plus the cuFFT work area).
+ * psr_pm_forces - device, asynchronous on cuda_stream, allocates nothing:
+ *   d_pos   device, n x 3 FP64, any real values (wrapped into [0, L)); a
+ *           particle with a non-finite coordinate deposits nothing and its
+ *           output is left unchanged
+ *   d_mass  device, n FP64, or NULL for equal masses 1/n
+ *   box     L, r_s, G (r_c unused)
+ *   flags   PSR_PM_ACCUMULATE: add to d_acc instead of overwriting it;
+ *           PSR_PM_NO_DECONVOLVE: keep the CIC windows
+ *   d_scratch device, >= psr_pm_scratch_bytes, 256-byte aligned, caller-owned
+ *   d_acc   device, n x 3 FP32, original particle order
+ *   Calls on one psr_pm must not overlap in time (they share its plans).
+ *   Mass is deposited with FP32 atomics, so the result varies with the
+ *   order of the additions at the level of FP32 rounding.
+ *   Errors: PSR_E_ARG, PSR_E_WORKSPACE, PSR_E_CUDA.
+ * psr_pm_free - host: destroy the plans (NULL is ignored).
+ */
+#define PSR_PM_ACCUMULATE 1
+#define PSR_PM_NO_DECONVOLVE 2
+typedef struct psr_pm psr_pm; /* opaque, host-owned */
+int psr_pm_create(int n_pm, psr_pm** out);
+int psr_pm_scratch_bytes(const psr_pm* pm, size_t* bytes);
+int psr_pm_forces(psr_pm* pm, const double* d_pos, const double* d_mass, int64_t n,
+                  const psr_box* box, int flags, void* d_scratch, size_t scratch_bytes,
+                  float* d_acc, void* cuda_stream);
+void psr_pm_free(psr_pm* pm);
+
 /* psr_free_leaves - host: free a handle (NULL is ignored). */
 void psr_free_leaves(psr_leaves* h);
 

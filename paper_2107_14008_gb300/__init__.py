@@ -16,7 +16,7 @@ from .capi import (PSR_ACC_FP64, PSR_ACC_KAHAN32, PSR_CUBIC, PSR_FP32_EXACT, PSR
                    PSR_FP64, PSR_KERNEL_AUTO, PSR_KERNEL_PACKED, PSR_KERNEL_SCALAR, PSR_LINEAR,
                    PSR_TAYLOR2, PSR_TAYLOR4, PsrError)
 
-__all__ = ["Options", "Leaves", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
+__all__ = ["Options", "Leaves", "PM", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
            "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_TAYLOR2", "PSR_TAYLOR4",
            "PSR_ACC_FP64", "PSR_ACC_KAHAN32",
            "PSR_KERNEL_AUTO", "PSR_KERNEL_SCALAR", "PSR_KERNEL_PACKED"]
@@ -300,6 +300,62 @@ class Leaves:
     def close(self):
         if getattr(self, "_h", None) is not None:
             capi.psr_free_leaves(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PM:
+    """Long-range particle-mesh accelerations on an n_pm^3 mesh (psr_pm_*):
+    the Gaussian-filtered complement of the short-range P2P force.  Holds the
+    cuFFT plans and a scratch tensor on one CUDA device."""
+
+    def __init__(self, n_pm, device=None):
+        import torch
+        self.n_pm = int(n_pm)
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self._h = capi.psr_pm_create(self.n_pm)
+        self.scratch = torch.empty(capi.psr_pm_scratch_bytes(self._h), dtype=torch.uint8,
+                                   device=self.device)
+
+    def forces(self, pos, mass, L, r_s, G=1.0, out=None, accumulate=False, deconvolve=True,
+               stream=None):
+        """Accelerations (n, 3) FP32 in the input order; with accumulate=True
+        they are added to `out` (e.g. the P2P result)."""
+        import torch
+        dev = self.device
+        p = pos.detach().to(device=dev, dtype=torch.float64).contiguous().reshape(-1, 3)
+        n = p.shape[0]
+        m = None
+        if mass is not None:
+            m = mass.detach().to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
+            if m.shape[0] != n:
+                raise ValueError("mass and pos lengths differ")
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs out")
+            out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        if out.dtype != torch.float32 or out.shape != (n, 3) or not out.is_contiguous() \
+                or out.device != dev:
+            raise ValueError("out must be a contiguous (n,3) float32 tensor on %s" % dev)
+        flags = (capi.PSR_PM_ACCUMULATE if accumulate else 0) | \
+            (0 if deconvolve else capi.PSR_PM_NO_DECONVOLVE)
+        with torch.cuda.device(dev):
+            capi.psr_pm_forces(self._h, p.data_ptr(), 0 if m is None else m.data_ptr(), n,
+                               _box(L, r_s, 1.0, G), flags, self.scratch.data_ptr(),
+                               self.scratch.numel(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            capi.psr_pm_free(self._h)
             self._h = None
 
     def __del__(self):

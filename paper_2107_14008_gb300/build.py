@@ -26,7 +26,7 @@ CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-fun
              "-ffp-contract=off",
              "-I" + os.path.join(ROOT, "include")]
 CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_f64.cu",
-              "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu"]
+              "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu", "pm.cu"]
 CXX_SOURCES = ["builder.cpp"]
 
 
@@ -83,7 +83,9 @@ def build(force=False, verbose=False):
     objs = [os.path.join(OUT, f + ".o") for f in CU_SOURCES + CXX_SOURCES]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + [
+            "-lpthread", "-L" + cudalib, "-lcufft", "-Xlinker", "-rpath=" + cudalib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stdout + r.stderr))

@@ -18,14 +18,15 @@ PSR_LINEAR, PSR_CUBIC, PSR_TAYLOR2, PSR_TAYLOR4 = 0, 1, 2, 3
 PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
 PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED = 0, 1, 2
 PSR_BUILD_NO_FP64 = 1
+PSR_PM_ACCUMULATE, PSR_PM_NO_DECONVOLVE = 1, 2
 
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
            "psr_check", "psr_table", "psr_autotune",
            "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
-           "psr_device_build", "psr_device_build_finish", "psr_free_leaves", "psr_last_error",
-           "psr_version"]
+           "psr_device_build", "psr_device_build_finish", "psr_pm_create", "psr_pm_scratch_bytes",
+           "psr_pm_forces", "psr_pm_free", "psr_free_leaves", "psr_last_error", "psr_version"]
 
 
 class psr_box(ctypes.Structure):
@@ -104,12 +105,18 @@ def lib():
                                    ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_int,
                                    ctypes.POINTER(vp)]
     L.psr_device_build_finish.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.psr_pm_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+    L.psr_pm_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.psr_pm_forces.argtypes = [vp, vp, vp, i64, ctypes.POINTER(psr_box), ctypes.c_int, vp,
+                                ctypes.c_size_t, vp, vp]
+    L.psr_pm_free.argtypes = [vp]
+    L.psr_pm_free.restype = None
     L.psr_free_leaves.argtypes = [vp]
     L.psr_free_leaves.restype = None
     L.psr_last_error.restype = ctypes.c_char_p
     L.psr_version.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("psr_free_leaves", "psr_last_error", "psr_version"):
+        if name not in ("psr_free_leaves", "psr_pm_free", "psr_last_error", "psr_version"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -219,6 +226,29 @@ def psr_device_build(d_pos, d_mass, n, box, max_leaf, flags, d_scratch, scratch_
 def psr_device_build_finish(h, d_ws, nbytes, stream):
     return check(lib().psr_device_build_finish(h, ctypes.c_void_p(d_ws), nbytes,
                                                ctypes.c_void_p(stream)))
+
+
+def psr_pm_create(n_pm):
+    h = ctypes.c_void_p()
+    check(lib().psr_pm_create(int(n_pm), ctypes.byref(h)))
+    return h
+
+
+def psr_pm_scratch_bytes(pm):
+    v = ctypes.c_size_t()
+    check(lib().psr_pm_scratch_bytes(pm, ctypes.byref(v)))
+    return v.value
+
+
+def psr_pm_forces(pm, d_pos, d_mass, n, box, flags, d_scratch, scratch_bytes, d_acc, stream):
+    return check(lib().psr_pm_forces(pm, ctypes.c_void_p(d_pos), ctypes.c_void_p(d_mass), n,
+                                     ctypes.byref(box), flags, ctypes.c_void_p(d_scratch),
+                                     scratch_bytes, ctypes.c_void_p(d_acc),
+                                     ctypes.c_void_p(stream)))
+
+
+def psr_pm_free(pm):
+    lib().psr_pm_free(pm)
 
 
 def psr_free_leaves(h):
