@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--adjoint-steps", type=int, default=3)
     p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--pm-steps", type=int, default=5,
+                   help="steps of the long-range PM part on the same box (0: skip)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
                    help="skip the precision study (one launch per T variant)")
     p.add_argument("--cpu-targets", type=int, default=100000,
@@ -480,6 +482,36 @@ def run_psr(args):
         e2e["host_build_path_ms_per_step"] = (time.perf_counter() - t2) * 1e3
         del lvh
 
+    # long-range PM part on the same box: CIC deposit, FFTs, Green's function,
+    # gradient, interpolation (one psr_pm_forces call per step)
+    pm_line = None
+    if args.pm_steps > 0:
+        pmo = psr.PM(b.n_pm, dev)
+        pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
+        mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
+        apm = pmo.forces(pos_d, mass_d, b.L, b.r_s, b.G)
+        torch.cuda.synchronize()
+        ep = []
+        for k in range(args.pm_steps):
+            flush.fill_(k & 255)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            pmo.forces(pos_d, mass_d, b.L, b.r_s, b.G, out=apm)
+            s1.record(stream)
+            ep.append((s0, s1))
+        torch.cuda.synchronize()
+        ms_pm = sum(a.elapsed_time(e) for a, e in ep) / args.pm_steps
+        pm_line = {"ms_per_step": ms_pm, "n_pm": b.n_pm, "particles": b.n,
+                   "particles_per_s": b.n / (ms_pm / 1e3),
+                   "kernels_per_step": "deposit, R2C, Green, 3 x (gradient, C2R), interpolation",
+                   "fraction_of_p2p_step": ms_pm / mean_ms}
+        if rank == 0 and not args.no_cpu_baseline and b.n <= (1 << 22):
+            from oracle import pm as opm
+            ref = opm.pm_forces(b.pos, b.mass, b.L, b.r_s, b.n_pm, b.G)
+            d = apm.double().cpu().numpy() - ref
+            pm_line["rel_rms_vs_fp64_oracle_mesh"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+        del pmo
+
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
         cb, err, tg, ref = cpu_baseline(b, acc32, args.cpu_targets, return_ref=True)
@@ -518,6 +550,7 @@ def run_psr(args):
         "fp64_path": fp64,
         "adjoint": adj,
         "batch": batch,
+        "pm_long_range": pm_line,
         "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
                         "sampled_targets": None if cb is None else args.cpu_targets},
