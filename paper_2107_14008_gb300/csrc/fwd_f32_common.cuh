@@ -35,6 +35,27 @@ namespace psr {
 
 enum { TM_EXACT = 0, TM_LINEAR = 1, TM_CUBIC = 2, TM_TAYLOR = 3 };
 
+// a * b + c clamped to [0, 1] in one instruction
+__device__ __forceinline__ float fma_sat(float a, float b, float c)
+{
+    float d;
+    asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Linear table (entries (A_k, N D_k) in shared memory).  The linear path
+// measures distances in units of x_c, so s = sat(r / x_c - 1/(2N)) = t / N
+// with t = u - 1/2 (u in table units) already clamped to [0, 1]: rint(s N) is
+// the interval (N, the zero sentinel, beyond the cutoff) and T = A_k + s N D_k.
+// Below u = 1/2 the clamp holds s at 0, which moves T by under 1e-8 (T is
+// flat there: T = 1 - O(x^3)).
+__device__ __forceinline__ float linear_T(float s, float nmax, unsigned tab_bias)
+{
+    const float fk = fmaf(s, nmax, kMagic);
+    const float2 c = lds_f2((unsigned)__float_as_int(fk) * 8u + tab_bias);
+    return fmaf(s, c.y, c.x);
+}
+
 // Paper's Taylor table (Section 3.3, Eq. int) about the nearest node: entry k
 // is two float4, (c0, c1, c2, c3) and (c4, 0, 0, 0), the expansion about x_k
 // in u - k (table units); nodes k = 0..N all real (x_N = x_c), so the cutoff,
@@ -263,6 +284,11 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
                            eval_T_exact(r2.y * rinv.y * xscale, x_c));
     } else if (TM == TM_TAYLOR) {  // t = u here (nearest node)
         return make_float2(taylor_T(t.x, nmax, tab_bias), taylor_T(t.y, nmax, tab_bias));
+    } else if (TM == TM_LINEAR) {  // t = s here (see linear_T)
+        const float2 fk = fma2(t, make_float2(nmax, nmax), make_float2(kMagic, kMagic));
+        const float2 ca = lds_f2((unsigned)__float_as_int(fk.x) * 8u + tab_bias);
+        const float2 cb = lds_f2((unsigned)__float_as_int(fk.y) * 8u + tab_bias);
+        return fma2(t, make_float2(ca.y, cb.y), make_float2(ca.x, cb.x));
     } else {
         t.x = fminf(t.x, nmax);
         t.y = fminf(t.y, nmax);
@@ -270,10 +296,7 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
         const float2 kf = add2(fk, make_float2(-kMagic, -kMagic));
         const float2 f = fma2(kf, make_float2(-1.0f, -1.0f), t);
         const unsigned ka = (unsigned)__float_as_int(fk.x), kb = (unsigned)__float_as_int(fk.y);
-        if (TM == TM_LINEAR) {  // (A_k, D_k): T = A_k + t D_k
-            const float2 ca = lds_f2(ka * 8u + tab_bias), cb = lds_f2(kb * 8u + tab_bias);
-            return fma2(t, make_float2(ca.y, cb.y), make_float2(ca.x, cb.x));
-        } else {
+        {
             const float4 ca = lds_f4(ka * 16u + tab_bias), cb = lds_f4(kb * 16u + tab_bias);
             return make_float2(fmaf(f.x, fmaf(f.x, fmaf(f.x, ca.w, ca.z), ca.y), ca.x),
                                fmaf(f.y, fmaf(f.y, fmaf(f.y, cb.w, cb.z), cb.y), cb.x));
@@ -304,7 +327,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
     const float nmax = (float)a.table_n;
     // working unit: table intervals (u = x N / x_c) for the table path, x itself
     // for the exact path
-    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    const float sc = TM == TM_EXACT ? 1.0f : TM == TM_LINEAR ? 1.0f / x_c : (float)a.table_n / x_c;
     const float xscale = 1.0f / sc;  // working unit -> x (exact path only)
     const float unit = bx.unit;
     const int4 ci = lcen[I];
@@ -331,6 +354,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
     const float2 eps2 = make_float2(eps, eps);
     // table coordinate: u - 1/2 (interval tables), u (Taylor: nearest node)
     const float2 mhalf = TM == TM_TAYLOR ? make_float2(0.0f, 0.0f) : make_float2(-0.5f, -0.5f);
+    const float soff = -0.5f / nmax;  // linear path: s = sat(r / x_c - 1/(2N))
     while (e0 < re) {
         int nst;
         e0 += stage_chunk<1>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
@@ -347,14 +371,16 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
                     const float2 dx = add2(px, ntx[r]), dy = add2(py, nty[r]), dz = add2(pz, ntz[r]);
                     const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
                     const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-                    const float2 t = fma2(r2, rinv, mhalf);
+                    const float2 t = TM == TM_LINEAR
+                                         ? make_float2(fma_sat(r2.x, rinv.x, soff), fma_sat(r2.y, rinv.y, soff))
+                                         : fma2(r2, rinv, mhalf);
                     const float2 Tv = eval_T2<TM>(t, r2, rinv, tab_bias, nmax, x_c, xscale);
                     const float2 w = mul2(mul2(mul2(mul2(pm, Tv), rinv), rinv), rinv);
                     fx[r] = fma2(w, dx, fx[r]);
                     fy[r] = fma2(w, dy, fy[r]);
                     fz[r] = fma2(w, dz, fz[r]);
                     if (COUNT) {
-                        const float uc = TM == TM_EXACT ? x_c : nmax;
+                        const float uc = TM == TM_EXACT ? x_c : TM == TM_LINEAR ? 1.0f : nmax;
                         const float ua = r2.x * rinv.x, ub = r2.y * rinv.y;
                         cnt += (act[r] && ua < uc && (dx.x != 0.0f || dy.x != 0.0f || dz.x != 0.0f));
                         cnt += (act[r] && ub < uc && (dx.y != 0.0f || dy.y != 0.0f || dz.y != 0.0f));
@@ -381,17 +407,13 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
 {
     if (TM == TM_EXACT) return eval_T_exact(r2 * rinv * xscale, x_c);
     if (TM == TM_TAYLOR) return taylor_T(t, nmax, tab_bias);  // t = u here
+    if (TM == TM_LINEAR) return linear_T(t, nmax, tab_bias);  // t = s here
     t = fminf(t, nmax);
     const float fk = t + kMagic;
     const unsigned k = (unsigned)__float_as_int(fk);
-    if (TM == TM_LINEAR) {  // (A_k, D_k): T = A_k + t D_k, no offset f needed
-        const float2 c = lds_f2(k * 8u + tab_bias);
-        return fmaf(t, c.y, c.x);
-    } else {
-        const float f = t - (fk - kMagic);
-        const float4 c = lds_f4(k * 16u + tab_bias);
-        return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
-    }
+    const float f = t - (fk - kMagic);
+    const float4 c = lds_f4(k * 16u + tab_bias);
+    return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }
 
 // Scalar-stream variant: stream s takes staged particles s, s+S, ... one at
@@ -413,7 +435,8 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
     const BoxDev& bx = a.boxes[li.z];
     const float x_c = bx.x_c;
     const float nmax = (float)a.table_n;
-    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    const float soff = -0.5f / nmax;  // linear path: s = sat(r / x_c - 1/(2N))
+    const float sc = TM == TM_EXACT ? 1.0f : TM == TM_LINEAR ? 1.0f / x_c : (float)a.table_n / x_c;
     const float xscale = 1.0f / sc;
     const float unit = bx.unit;
     const int4 ci = lcen[I];
@@ -449,15 +472,16 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
                     float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
                     float rinv = rsqrt_ftz(r2);
-                    float Tv = eval_T1<TM>(fmaf(r2, rinv, TM == TM_TAYLOR ? 0.0f : -0.5f), r2,
-                                           rinv, tab_bias, nmax, x_c, xscale);
+                    const float t = TM == TM_LINEAR ? fma_sat(r2, rinv, soff)
+                                                    : fmaf(r2, rinv, TM == TM_TAYLOR ? 0.0f : -0.5f);
+                    float Tv = eval_T1<TM>(t, r2, rinv, tab_bias, nmax, x_c, xscale);
                     float w = p.w * Tv * rinv * rinv * rinv;
                     fx[r] = fmaf(w, dx, fx[r]);
                     fy[r] = fmaf(w, dy, fy[r]);
                     fz[r] = fmaf(w, dz, fz[r]);
                     if (COUNT) {
                         const float u = r2 * rinv;
-                        const float uc = TM == TM_EXACT ? x_c : nmax;
+                        const float uc = TM == TM_EXACT ? x_c : TM == TM_LINEAR ? 1.0f : nmax;
                         cnt += (act[r] && u < uc && (dx != 0.0f || dy != 0.0f || dz != 0.0f));
                     }
                 }
@@ -504,7 +528,7 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
             const float4 v = g[i];
             if (TM == TM_LINEAR)
-                reinterpret_cast<float2*>(smem)[i] = make_float2(v.z, v.y);  // (A_k, D_k)
+                reinterpret_cast<float2*>(smem)[i] = make_float2(v.z, v.y * (float)a.table_n);  // (A_k, N D_k)
             else
                 reinterpret_cast<float4*>(smem)[i] = v;
         }
