@@ -579,8 +579,10 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 template <int TM, int ACC, bool COUNT, bool PK>
 static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    auto k = a.max_leaf > 32 ? p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>
-                             : p2p_fwd_f32_kernel<TM, ACC, COUNT, false, PK>;
+    // The scalar kernel always carries the two-targets-per-lane path: leaves of
+    // 11-12 and 17-20 particles fill more lanes with it (prefer_two_per_lane).
+    auto k = (!PK || a.max_leaf > 32) ? p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>
+                                      : p2p_fwd_f32_kernel<TM, ACC, COUNT, false, PK>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -615,7 +617,7 @@ int launch_fwd_f32_variant(const FwdArgs& a, int precision, size_t smem, cudaStr
 template <bool PK>
 const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_leaf)
 {
-#define PSR_PICK(TM, ACC) (max_leaf > 32 ? (const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK> \
+#define PSR_PICK(TM, ACC) ((!PK || max_leaf > 32) ? (const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK> \
                                          : (const void*)p2p_fwd_f32_kernel<TM, ACC, false, false, PK>)
     if (precision == PSR_FP32_EXACT)
         return accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
