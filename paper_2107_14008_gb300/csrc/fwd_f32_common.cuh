@@ -214,10 +214,13 @@ __device__ __forceinline__ void finish_item(const FwdArgs& a, int4 li, Acc3<ACC>
                                             const bool* act, int lane, int s, int q, int S, int T,
                                             float gout, float4* __restrict__ stage)
 {
+    // Each target slot r reduces through its own region of the staging buffer
+    // (768 B; two slots fit the smallest per-warp buffer, 64 + 32 float4), with
+    // volatile accesses, so one slot's stores cannot overtake another's loads.
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (ACC == PSR_ACC_FP64) {
-            double* red = reinterpret_cast<double*>(stage);
+            volatile double* red = reinterpret_cast<volatile double*>(stage) + 96 * r;
             red[3 * lane + 0] = acc[r].x;
             red[3 * lane + 1] = acc[r].y;
             red[3 * lane + 2] = acc[r].z;
@@ -236,7 +239,7 @@ __device__ __forceinline__ void finish_item(const FwdArgs& a, int4 li, Acc3<ACC>
                 out[2] = (float)(sz * (double)gout);
             }
         } else {
-            float* red = reinterpret_cast<float*>(stage);
+            volatile float* red = reinterpret_cast<volatile float*>(stage) + 192 * r;
             red[6 * lane + 0] = acc[r].sx;
             red[6 * lane + 1] = acc[r].cx;
             red[6 * lane + 2] = acc[r].sy;
@@ -248,7 +251,7 @@ __device__ __forceinline__ void finish_item(const FwdArgs& a, int4 li, Acc3<ACC>
                 float sx = acc[r].sx, cx = acc[r].cx, sy = acc[r].sy, cy = acc[r].cy;
                 float sz = acc[r].sz, cz = acc[r].cz, u, v;
                 for (int t = 1; t < S; ++t) {
-                    const float* o = red + 6 * (lane + t * T);
+                    const volatile float* o = red + 6 * (lane + t * T);
                     two_sum(sx, o[0], u, v); sx = u; cx += o[1] + v;
                     two_sum(sy, o[2], u, v); sy = u; cy += o[3] + v;
                     two_sum(sz, o[4], u, v); sz = u; cz += o[5] + v;

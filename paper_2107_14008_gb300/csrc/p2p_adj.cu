@@ -155,11 +155,15 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
     // dL/dx = G/(8 r_s^3) sc^3 sum,  dL/dm = -G/(4 r_s^2) sc^2 sum
     const float gx = bx.g_adj * sc * sc * sc;
     const float gm = -bx.g_adjm * sc * sc;
-    // combine the S stream partials through the staging buffer
+    // Combine the S stream partials through the staging buffer: each target
+    // slot r has its own region (1 KB) and the accesses are volatile, so no
+    // slot's writes can meet another slot's reads whatever the compiler's
+    // ordering (a shared region let the second slot's stores overtake the
+    // first slot's loads).
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (ACC == PSR_ACC_FP64) {
-            double* red = reinterpret_cast<double*>(stage);
+            volatile double* red = reinterpret_cast<volatile double*>(stage) + 128 * r;
 #pragma unroll
             for (int i = 0; i < 4; ++i) red[4 * lane + i] = acc[r].d[i];
             __syncwarp();
@@ -176,7 +180,7 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
                 if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (float)(t4[3] * (double)gm);
             }
         } else {
-            float* red = reinterpret_cast<float*>(stage);
+            volatile float* red = reinterpret_cast<volatile float*>(stage) + 256 * r;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 red[8 * lane + 2 * i] = acc[r].s[i];
@@ -193,7 +197,7 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
                 for (int t = 1; t < S; ++t)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const float* o = red + 8 * (lane + t * T) + 2 * i;
+                        const volatile float* o = red + 8 * (lane + t * T) + 2 * i;
                         two_sum(hi[i], o[0], u, v);
                         hi[i] = u;
                         lo[i] += o[1] + v;
@@ -428,7 +432,8 @@ size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 template <int TM, int ACC>
 static int launch_adj_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    auto k = a.max_leaf > 32 ? p2p_adj_f32_kernel<TM, ACC, true> : p2p_adj_f32_kernel<TM, ACC, false>;
+    // always with the two-targets-per-lane path (mid-size leaves fill more lanes)
+    auto k = p2p_adj_f32_kernel<TM, ACC, true>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -479,8 +484,7 @@ int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf,
         f = wide ? (const void*)p2p_adj_f64_kernel<true> : (const void*)p2p_adj_f64_kernel<false>;
     } else {
         smem = adj_f32_smem(precision, interp, table_n, warps, cap);
-#define PSR_PICK(TM, ACC) (wide ? (const void*)p2p_adj_f32_kernel<TM, ACC, true> \
-                                : (const void*)p2p_adj_f32_kernel<TM, ACC, false>)
+#define PSR_PICK(TM, ACC) ((const void*)p2p_adj_f32_kernel<TM, ACC, true>)
         if (precision == PSR_FP32_EXACT)
             f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
         else if (interp == PSR_LINEAR)

@@ -528,3 +528,22 @@ def test_taylor_table_is_forward_only_and_runs_without_allocation():
                                 torch.cuda.current_stream().cuda_stream)
     assert torch.equal(a3, a2)
     lv.check()
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered"])
+@pytest.mark.parametrize("name,kw", [("lin1024", dict(precision=psr.PSR_FP32_TABLE)),
+                                     ("exact", dict(precision=psr.PSR_FP32_EXACT))])
+@pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
+@pytest.mark.parametrize("max_leaf", [16, 64])
+def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf):
+    """The FP32 adjoint's two-targets-per-lane path (leaves of 11-12 and 17-20
+    particles at max_leaf 16/32, every leaf above 32 at max_leaf 64), both
+    accumulations: every target slot of a lane must reduce correctly."""
+    b = CASES[case]()
+    cot = synth.cotangent(b.n, 6)
+    gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(accum=accum, **kw))
+    lv.check()
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4, name
+    assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
