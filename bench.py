@@ -407,6 +407,18 @@ def run_psr(args):
                 "dL_dx": float(torch.sqrt((dg * dg).sum() / (g64 * g64).sum())),
                 "dL_dm": float(torch.sqrt((dm * dm).sum() / (m64 * m64).sum()))}
         lv.check()
+        if rank == 0 and not args.no_cpu_baseline:
+            # the FP32 adjoint against the FP64 oracle on sampled targets
+            import oracle
+            tg = np.sort(np.random.default_rng(11).choice(b.n, min(1000, b.n), replace=False))
+            gref, mref = oracle.adjoint(b.pos, b.mass, cot.double().cpu().numpy(), b.L, b.r_s,
+                                        b.r_c, b.G, targets=tg, cells=True)
+            dg = gp.double().cpu().numpy()[tg] - gref
+            dm = gm.double().cpu().numpy()[tg] - mref
+            adj["rel_rms_vs_fp64_oracle_sampled"] = {
+                "targets": int(tg.size),
+                "dL_dx": float(np.sqrt(np.sum(dg * dg) / np.sum(gref * gref))),
+                "dL_dm": float(np.sqrt(np.sum(dm * dm) / np.sum(mref * mref)))}
 
     # the precision study: every T variant and accumulation, one launch each
     variants = []
