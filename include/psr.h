@@ -411,6 +411,51 @@ int psr_pm_forces(psr_pm* pm, const double* d_pos, const double* d_mass, int64_t
                   float* d_acc, void* cuda_stream);
 void psr_pm_free(psr_pm* pm);
 
+/* ------------------------------------------- truncated multipole part */
+/*
+ * The truncated multipole operators of the PM-FMM short range (paper,
+ * Section 2: P2M, M2L with the truncated prefactors f_(n), L2P).  Kernel
+ * psi(r) = erfc(r / 2 r_s) / r, f_(k) = (1/r d/dr)^k psi from the paper's
+ * closed form, derivative tensors D_n(R) = d^n psi(R) from the f_(k).
+ * Cells are CSR ranges [first[c], first[c+1]) of a particle array.
+ * Expansions to order p (1 <= p <= 6), multi-indices |n| <= p in graded
+ * order (|n|, then n1 descending, then n2 descending), coefficients scaled
+ * by a caller-chosen length h (the cell size is a good choice: h^(2k+1)
+ * f_(k) then stays within FP32 for well-separated cells):
+ *   Mh_m = sum_j m_j ((z_A - x_j)/h)^m / m!                       (P2M)
+ *   Lh_n = sum_{|m| <= p-|n|} Mh_m h^(|n|+|m|+1) D_{n+m}(z_B - z_A) (M2L)
+ *   a_c(x) = (G/h^2) sum_{|k| <= p-1} Lh_{k+e_c} ((x - z_B)/h)^k / k!  (L2P)
+ * so that a(x) approximates G sum_j m_j grad psi(x - x_j) over the source
+ * cells (the smooth truncated kernel, no hard cutoff).  All three are
+ * asynchronous on cuda_stream and allocate nothing; FP32 coefficients.
+ *
+ * psr_fmm_ncoef - host: (p+1)(p+2)(p+3)/6 coefficients per cell.
+ * psr_fmm_p2m - d_first (ncell+1) int64, d_pos n x 3 FP64, d_mass n FP64 or
+ *   NULL for 1/n, d_centre ncell x 3 FP64 -> d_M ncell x ncoef FP32.
+ * psr_fmm_m2l - target cells t: entries d_pairs[d_rowptr[t] .. d_rowptr[t+1])
+ *   = (source cell << 5) | image code (nx+1)*9 + (ny+1)*3 + (nz+1), the source
+ *   centre taken at c_s + n L (box->L); box->r_s sets the kernel.  Writes
+ *   d_L ntarget x ncoef.  d_status (device uint32, may be NULL) gets bit 0
+ *   for an entry out of range and bit 1 for coincident centres (both
+ *   skipped).
+ * psr_fmm_l2p - accelerations of the particles of each cell from its local
+ *   coefficients, times box->G; PSR_FMM_ACCUMULATE adds into d_acc (n x 3
+ *   FP32) instead of overwriting.
+ * Errors: PSR_E_ARG (order, scale, NULL, counts), PSR_E_CUDA.
+ */
+#define PSR_FMM_ACCUMULATE 1
+int psr_fmm_ncoef(int p, int* ncoef);
+int psr_fmm_p2m(int p, double h, int64_t n, int64_t ncell, const int64_t* d_first,
+                const double* d_pos, const double* d_mass, const double* d_centre, float* d_M,
+                void* cuda_stream);
+int psr_fmm_m2l(int p, double h, const psr_box* box, int64_t ntarget, int64_t nsource,
+                const int64_t* d_rowptr, const uint32_t* d_pairs, const double* d_centre_t,
+                const double* d_centre_s, const float* d_M, float* d_L, unsigned* d_status,
+                void* cuda_stream);
+int psr_fmm_l2p(int p, double h, const psr_box* box, int64_t ncell, const int64_t* d_first,
+                const double* d_pos, const double* d_centre, const float* d_L, float* d_acc,
+                int flags, void* cuda_stream);
+
 /* psr_free_leaves - host: free a handle (NULL is ignored). */
 void psr_free_leaves(psr_leaves* h);
 

@@ -26,7 +26,7 @@ CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-fun
              "-ffp-contract=off",
              "-I" + os.path.join(ROOT, "include")]
 CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_f64.cu",
-              "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu", "pm.cu"]
+              "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu", "pm.cu", "fmm.cu"]
 CXX_SOURCES = ["builder.cpp"]
 
 

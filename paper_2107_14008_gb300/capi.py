@@ -19,6 +19,7 @@ PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
 PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED = 0, 1, 2
 PSR_BUILD_NO_FP64 = 1
 PSR_PM_ACCUMULATE, PSR_PM_NO_DECONVOLVE = 1, 2
+PSR_FMM_ACCUMULATE = 1
 
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
@@ -26,7 +27,8 @@ EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr
            "psr_check", "psr_table", "psr_autotune",
            "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
            "psr_device_build", "psr_device_build_finish", "psr_pm_create", "psr_pm_scratch_bytes",
-           "psr_pm_forces", "psr_pm_free", "psr_free_leaves", "psr_last_error", "psr_version"]
+           "psr_pm_forces", "psr_pm_free", "psr_fmm_ncoef", "psr_fmm_p2m", "psr_fmm_m2l",
+           "psr_fmm_l2p", "psr_free_leaves", "psr_last_error", "psr_version"]
 
 
 class psr_box(ctypes.Structure):
@@ -111,6 +113,12 @@ def lib():
                                 ctypes.c_size_t, vp, vp]
     L.psr_pm_free.argtypes = [vp]
     L.psr_pm_free.restype = None
+    L.psr_fmm_ncoef.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.psr_fmm_p2m.argtypes = [ctypes.c_int, ctypes.c_double, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.psr_fmm_m2l.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(psr_box), i64, i64,
+                              vp, vp, vp, vp, vp, vp, vp, vp]
+    L.psr_fmm_l2p.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(psr_box), i64, vp, vp,
+                              vp, vp, vp, ctypes.c_int, vp]
     L.psr_free_leaves.argtypes = [vp]
     L.psr_free_leaves.restype = None
     L.psr_last_error.restype = ctypes.c_char_p
@@ -249,6 +257,34 @@ def psr_pm_forces(pm, d_pos, d_mass, n, box, flags, d_scratch, scratch_bytes, d_
 
 def psr_pm_free(pm):
     lib().psr_pm_free(pm)
+
+
+def psr_fmm_ncoef(p):
+    v = ctypes.c_int()
+    check(lib().psr_fmm_ncoef(int(p), ctypes.byref(v)))
+    return v.value
+
+
+def _vp(x):
+    return ctypes.c_void_p(x or None)
+
+
+def psr_fmm_p2m(p, h, n, ncell, d_first, d_pos, d_mass, d_centre, d_M, stream):
+    return check(lib().psr_fmm_p2m(int(p), float(h), n, ncell, _vp(d_first), _vp(d_pos),
+                                   _vp(d_mass), _vp(d_centre), _vp(d_M), _vp(stream)))
+
+
+def psr_fmm_m2l(p, h, box, ntarget, nsource, d_rowptr, d_pairs, d_ct, d_cs, d_M, d_L, d_status,
+                stream):
+    return check(lib().psr_fmm_m2l(int(p), float(h), ctypes.byref(box), ntarget, nsource,
+                                   _vp(d_rowptr), _vp(d_pairs), _vp(d_ct), _vp(d_cs), _vp(d_M),
+                                   _vp(d_L), _vp(d_status), _vp(stream)))
+
+
+def psr_fmm_l2p(p, h, box, ncell, d_first, d_pos, d_centre, d_L, d_acc, flags, stream):
+    return check(lib().psr_fmm_l2p(int(p), float(h), ctypes.byref(box), ncell, _vp(d_first),
+                                   _vp(d_pos), _vp(d_centre), _vp(d_L), _vp(d_acc), int(flags),
+                                   _vp(stream)))
 
 
 def psr_free_leaves(h):
