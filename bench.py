@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--adjoint-steps", type=int, default=3)
     p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--fmm-steps", type=int, default=3,
+                   help="steps of the truncated multipole operators on the leaves (0: skip)")
+    p.add_argument("--fmm-order", type=int, default=4)
     p.add_argument("--pm-steps", type=int, default=5,
                    help="steps of the long-range PM part on the same box (0: skip)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
@@ -196,6 +199,95 @@ def run_batch(args, psr, torch, dev, stream, flush):
                            "warps_per_block": best.warps_per_block,
                            "source_tile": best.source_tile},
             "path": "FP32, linear 1024 table, FP64 fold"}
+
+
+def run_fmm(args, torch, dev, b, lv, stream, flush, check):
+    """Truncated multipole operators (P2M, M2L with the f_(n) prefactors, L2P)
+    on the workload's leaves: P2M on every leaf; M2L on the leaf pairs of the
+    near-field list whose cell centres are at least 1.5 x the summed cell
+    sides apart (a multipole acceptance criterion), for the first 5000
+    target leaves; L2P on those targets."""
+    import numpy as np
+    from paper_2107_14008_gb300 import capi
+    p = args.fmm_order
+    A = lv.host_arrays()
+    leaf, lcen, rowptr, pairs = A["leaf"], A["lcen"], A["rowptr"], A["pairs"]
+    nl = len(leaf)
+    centres = lcen[:, :3].astype(np.float64) * (b.L / 2.0 ** 22)
+    side = b.L / 2.0 ** lcen[:, 3].astype(np.float64)
+    first = np.concatenate([leaf[:, 0], [b.n]]).astype(np.int64)
+    perm = lv.perm
+    spos = np.mod(b.pos, b.L)[perm]  # wrapped, leaf (Morton) order
+    smass = np.asarray(b.mass)[perm]
+    nt = min(nl, 5000)
+    e1 = int(rowptr[nt])
+    tgt = np.repeat(np.arange(nt), np.diff(rowptr[:nt + 1]))
+    src = (pairs[:e1] >> 5).astype(np.int64)
+    code = (pairs[:e1] & 31).astype(np.int64)
+    sh = np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], axis=1) * b.L
+    dist = np.linalg.norm(centres[tgt] - centres[src] - sh, axis=1)
+    far = dist >= 1.5 * (side[tgt] + side[src])
+    frow = np.concatenate([[0], np.cumsum(np.bincount(tgt[far], minlength=nt))]).astype(np.int64)
+    fpairs = pairs[:e1][far]
+    h = float(np.median(side))
+    box = capi.psr_box(b.L, b.r_s, b.r_c, b.G)
+    nc = capi.psr_fmm_ncoef(p)
+    d = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    pos_d, mass_d = d(spos, torch.float64), d(smass, torch.float64)
+    first_d, cen_d = d(first, torch.int64), d(centres, torch.float64)
+    rp_d, pr_d = d(frow, torch.int64), d(fpairs.view(np.int32), torch.int32)
+    M = torch.empty((nl, nc), dtype=torch.float32, device=dev)
+    Lc = torch.empty((nt, nc), dtype=torch.float32, device=dev)
+    acc = torch.zeros((b.n, 3), dtype=torch.float32, device=dev)
+    st = stream.cuda_stream
+
+    def step():
+        capi.psr_fmm_p2m(p, h, b.n, nl, first_d.data_ptr(), pos_d.data_ptr(), mass_d.data_ptr(),
+                         cen_d.data_ptr(), M.data_ptr(), st)
+        ev[1].record(stream)
+        capi.psr_fmm_m2l(p, h, box, nt, nl, rp_d.data_ptr(), pr_d.data_ptr(), cen_d.data_ptr(),
+                         cen_d.data_ptr(), M.data_ptr(), Lc.data_ptr(), 0, st)
+        ev[2].record(stream)
+        capi.psr_fmm_l2p(p, h, box, nt, first_d.data_ptr(), pos_d.data_ptr(), cen_d.data_ptr(),
+                         Lc.data_ptr(), acc.data_ptr(), 0, st)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    step()
+    torch.cuda.synchronize()
+    t = np.zeros(3)
+    for k in range(args.fmm_steps):
+        flush.fill_(k & 255)
+        ev[0].record(stream)
+        step()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    t /= args.fmm_steps
+    nfar = int(far.sum())
+    out = {"order": p, "scale_h": h, "leaves": nl, "target_leaves": nt, "m2l_entries": nfar,
+           "near_entries_of_those_rows": e1 - nfar, "p2m_ms": t[0], "m2l_ms": t[1],
+           "l2p_ms": t[2], "m2l_entries_per_s": nfar / (t[1] / 1e3),
+           "mac": "centre distance >= 1.5 x (side_I + side_J)"}
+    if check:
+        from oracle import fmm as ofmm
+        got = acc.double().cpu().numpy()
+        rows = [r for r in np.random.default_rng(3).permutation(nt)[:200]
+                if frow[r + 1] > frow[r]][:3]
+        num = den = 0.0
+        for r in rows:
+            tp = spos[first[r]:first[r + 1]]
+            sp, sm = [], []
+            for e in range(frow[r], frow[r + 1]):
+                s_, c_ = int(fpairs[e]) >> 5, int(fpairs[e]) & 31
+                shv = np.array([c_ // 9 - 1, (c_ // 3) % 3 - 1, c_ % 3 - 1]) * b.L
+                sp.append(spos[first[s_]:first[s_ + 1]] + shv)
+                sm.append(smass[first[s_]:first[s_ + 1]])
+            ref = ofmm.direct(np.concatenate(sp), np.concatenate(sm), tp, b.r_s, b.G)
+            num += np.sum((got[first[r]:first[r + 1]] - ref) ** 2)
+            den += np.sum(ref ** 2)
+        out["rel_rms_vs_direct_sampled"] = float(np.sqrt(num / den)) if den > 0 else None
+        out["sampled_target_leaves"] = len(rows)
+    return out
 
 
 def cpu_baseline(b, acc_gpu, n_targets, seed=2024, return_ref=False):
@@ -524,6 +616,11 @@ def run_psr(args):
             pm_line["rel_rms_vs_fp64_oracle_mesh"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
         del pmo
 
+    fmm_line = None
+    if args.fmm_steps > 0 and b.n <= (1 << 22):
+        fmm_line = run_fmm(args, torch, dev, b, lv, stream, flush,
+                           rank == 0 and not args.no_cpu_baseline)
+
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
         cb, err, tg, ref = cpu_baseline(b, acc32, args.cpu_targets, return_ref=True)
@@ -563,6 +660,7 @@ def run_psr(args):
         "adjoint": adj,
         "batch": batch,
         "pm_long_range": pm_line,
+        "fmm_operators": fmm_line,
         "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
                         "sampled_targets": None if cb is None else args.cpu_targets},

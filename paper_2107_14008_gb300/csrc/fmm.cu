@@ -45,12 +45,11 @@ __device__ __forceinline__ int cidx(int a, int b, int c)
     return K * (K + 1) * (K + 2) / 6 + (K - a) * (K - a + 1) / 2 + (K - a - b);
 }
 
-__device__ __forceinline__ float ffact(int n)
-{
-    float f = 1.0f;
-    for (int i = 2; i <= n; ++i) f *= (float)i;
-    return f;
-}
+__constant__ float c_fact[kMaxDOrder + 1] = {1.f, 1.f, 2.f, 6.f, 24.f, 120.f, 720.f, 5040.f,
+                                             40320.f, 362880.f, 3628800.f, 39916800.f,
+                                             479001600.f};
+
+__device__ __forceinline__ float ffact(int n) { return c_fact[n]; }
 
 // phi[k] = h^(2k+1) f_(k)(r) for k = 0..kmax from the closed form, written
 // with x = r / 2 r_s, rho = h / r_s and w = rho / x = 2h / r so that no
@@ -105,9 +104,9 @@ __device__ void scaled_derivatives(const float Rh[3], float x, float rho, int or
                     for (int j2 = 0; 2 * j2 <= n2; ++j2)
                         for (int j3 = 0; 2 * j3 <= n3; ++j3) {
                             const float c =
-                                ffact(n1) / (exp2f((float)j1) * ffact(j1) * ffact(n1 - 2 * j1)) *
-                                ffact(n2) / (exp2f((float)j2) * ffact(j2) * ffact(n2 - 2 * j2)) *
-                                ffact(n3) / (exp2f((float)j3) * ffact(j3) * ffact(n3 - 2 * j3));
+                                ffact(n1) / ((float)(1 << j1) * ffact(j1) * ffact(n1 - 2 * j1)) *
+                                ffact(n2) / ((float)(1 << j2) * ffact(j2) * ffact(n2 - 2 * j2)) *
+                                ffact(n3) / ((float)(1 << j3) * ffact(j3) * ffact(n3 - 2 * j3));
                             s += c * pw[0][n1 - 2 * j1] * pw[1][n2 - 2 * j2] * pw[2][n3 - 2 * j3] *
                                  phi[K - j1 - j2 - j3];
                         }
@@ -142,21 +141,24 @@ __global__ void k_p2m(int p, double inv_h, int64_t ncell, const int64_t* __restr
 }
 
 // Lh_n = sum over the row's (source, image) entries of sum_m Mh_m Dh_{n+m},
-// one thread per target cell.  Entry = (source << 5) | image code, the code
-// (nx+1)*9 + (ny+1)*3 + (nz+1); the source centre is taken at c_s + n L.
+// one warp per target cell: the lanes take the row's entries in turn and the
+// 32 partial expansions are summed by shuffles.  Entry = (source << 5) |
+// image code, the code (nx+1)*9 + (ny+1)*3 + (nz+1); the source centre is
+// taken at c_s + n L.
 __global__ void k_m2l(int p, double inv_h, float x_per_h, float rho, double L, int64_t ntarget,
                       int64_t nsource, const int64_t* __restrict__ rowptr,
                       const uint32_t* __restrict__ pairs, const double* __restrict__ ct,
                       const double* __restrict__ cs, const float* __restrict__ M,
                       float* __restrict__ Lout, unsigned* __restrict__ err)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= ntarget) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= ntarget) return;  // whole warps only
     const int nc = ncoef(p);
     float acc[kMaxCoef];
     for (int i = 0; i < nc; ++i) acc[i] = 0.0f;
     float D[kMaxD];
-    for (int64_t e = rowptr[t]; e < rowptr[t + 1]; ++e) {
+    for (int64_t e = rowptr[t] + lane; e < rowptr[t + 1]; e += 32) {
         const uint32_t ent = pairs[e];
         const int64_t s = ent >> 5;
         const int code = ent & 31;
@@ -191,7 +193,11 @@ __global__ void k_m2l(int p, double inv_h, float x_per_h, float rho, double L, i
                     acc[cidx(n1, n2, n3)] += v;
                 }
     }
-    for (int i = 0; i < nc; ++i) Lout[t * nc + i] = acc[i];
+    for (int i = 0; i < nc; ++i) {
+        float v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) Lout[t * nc + i] = v;
+    }
 }
 
 // a_c(x) = (G / h^2) sum_{|k| <= p-1} Lh_{k+e_c} ((x - z_B)/h)^k / k!, one
@@ -294,7 +300,7 @@ int psr_fmm_m2l(int p, double h, const psr_box* box, int64_t ntarget, int64_t ns
         return ffail(PSR_E_ARG, "null argument or negative count");
     if (ntarget == 0) return PSR_OK;
     const double rho = h / box->r_s;
-    k_m2l<<<fblk(ntarget, 64), 64, 0, (cudaStream_t)stream>>>(
+    k_m2l<<<fblk(ntarget * 32, 128), 128, 0, (cudaStream_t)stream>>>(
         p, 1.0 / h, (float)(0.5 * rho), (float)rho, box->L, ntarget, nsource, d_rowptr, d_pairs,
         d_centre_t, d_centre_s, d_M, d_L, d_status);
     return fcuda("M2L kernel");
