@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--fmm-steps", type=int, default=3,
                    help="steps of the truncated multipole operators on the leaves (0: skip)")
     p.add_argument("--fmm-order", type=int, default=4)
+    p.add_argument("--split-steps", type=int, default=3,
+                   help="timed steps of the split short range (P2P near + multipole far)")
+    p.add_argument("--split-theta", type=float, default=0.5)
+    p.add_argument("--split-orders", default="4,6")
     p.add_argument("--pm-steps", type=int, default=5,
                    help="steps of the long-range PM part on the same box (0: skip)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
@@ -201,6 +205,22 @@ def run_batch(args, psr, torch, dev, stream, flush):
             "path": "FP32, linear 1024 table, FP64 fold"}
 
 
+def m2l_flops_per_entry(p):
+    """Algorithmic FP32 flops of one M2L entry: 2 per multiply-add of the
+    contraction L_n += M_m D_(n+m) over |n + m| <= p, 2 per term of the
+    derivative tensors D_k = sum_j c u^(k-2j) phi_(|k|-|j|), 1 per tensor
+    rescale."""
+    contraction = terms = nd = 0
+    for K in range(p + 1):
+        for a in range(K + 1):
+            for b in range(K - a + 1):
+                c = K - a - b
+                contraction += (a + 1) * (b + 1) * (c + 1)
+                terms += (a // 2 + 1) * (b // 2 + 1) * (c // 2 + 1)
+                nd += 1
+    return 2 * contraction + 2 * terms + nd
+
+
 def run_fmm(args, torch, dev, b, lv, stream, flush, check):
     """Truncated multipole operators (P2M, M2L with the f_(n) prefactors, L2P)
     on the workload's leaves: P2M on every leaf; M2L on the leaf pairs of the
@@ -267,6 +287,8 @@ def run_fmm(args, torch, dev, b, lv, stream, flush, check):
     out = {"order": p, "scale_h": h, "leaves": nl, "target_leaves": nt, "m2l_entries": nfar,
            "near_entries_of_those_rows": e1 - nfar, "p2m_ms": t[0], "m2l_ms": t[1],
            "l2p_ms": t[2], "m2l_entries_per_s": nfar / (t[1] / 1e3),
+           "m2l_flops_per_entry": m2l_flops_per_entry(p),
+           "m2l_tflops": m2l_flops_per_entry(p) * nfar / (t[1] / 1e3) / 1e12,
            "mac": "centre distance >= 1.5 x (side_I + side_J)"}
     if check:
         from oracle import fmm as ofmm
@@ -288,6 +310,76 @@ def run_fmm(args, torch, dev, b, lv, stream, flush, check):
         out["rel_rms_vs_direct_sampled"] = float(np.sqrt(num / den)) if den > 0 else None
         out["sampled_target_leaves"] = len(rows)
     return out
+
+
+def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evaluated):
+    """The short range with the multipole split (psr_device_build_split):
+    P2P (FP32 table, the headline options) over the near entries plus
+    psr_fmm_forces (P2M, M2L, L2P) over the well-separated ones, against the
+    plain P2P step over the full list.  Returns the bench fields and the
+    total accelerations per order, for the oracle comparison."""
+    pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
+    mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
+    theta = args.split_theta
+    lv = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
+                                 theta=theta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lvb = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
+                                      theta=theta)
+        torch.cuda.synchronize()
+        del lvb
+    build_ms = (time.perf_counter() - t0) / 3 * 1e3
+    inf = lv.info
+    acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    orders = [int(x) for x in args.split_orders.split(",") if x]
+    nl = int(inf.n_leaves)
+    scratch = torch.empty(2 * nl * ((capi_ncoef(max(orders)) + 3) // 4 * 4), dtype=torch.float32,
+                          device=dev)
+    out = {"theta": theta, "leaves": nl, "near_entries": int(inf.n_pairs),
+           "far_entries": int(inf.n_far), "evaluated_near": int(inf.evaluated_pairs),
+           "evaluated_full": int(full_evaluated),
+           "p2p_interactions_moved_to_m2l": 1.0 - inf.evaluated_pairs / full_evaluated,
+           "device_build_split_ms": build_ms, "full_p2p_ms": full_ms,
+           "acceptance": "theta |R| >= rho_I + rho_J (box half-diagonals), both boxes "
+                         "wholly within r_c", "orders": []}
+    totals = {}
+    for p in orders:
+        def step():
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            lv.forces(opts, out=acc)
+            e[1].record(stream)
+            lv.fmm_forces(p, out=acc, accumulate=True, scratch=scratch, status=status)
+            e[2].record(stream)
+            return e
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        tn = tf = 0.0
+        for k in range(args.split_steps):
+            flush.fill_(k & 255)
+            e = step()
+            torch.cuda.synchronize()
+            tn += e[0].elapsed_time(e[1])
+            tf += e[1].elapsed_time(e[2])
+        tn /= args.split_steps
+        tf /= args.split_steps
+        lv.check()
+        totals[p] = acc.double().cpu().numpy()
+        out["orders"].append({"order": p, "p2p_near_ms": tn, "fmm_far_ms": tf,
+                              "short_range_ms": tn + tf, "speedup_vs_full_p2p": full_ms / (tn + tf),
+                              "m2l_entries_per_s_upper_bound_time": inf.n_far / (tf / 1e3),
+                              "status": int(status.item())})
+    del lv
+    return out, totals
+
+
+def capi_ncoef(p):
+    from paper_2107_14008_gb300 import capi
+    return capi.psr_fmm_ncoef(p)
 
 
 def cpu_baseline(b, acc_gpu, n_targets, seed=2024, return_ref=False):
@@ -621,9 +713,18 @@ def run_psr(args):
         fmm_line = run_fmm(args, torch, dev, b, lv, stream, flush,
                            rank == 0 and not args.no_cpu_baseline)
 
+    split_line = split_acc = None
+    if args.split_steps > 0 and b.n <= (1 << 22):
+        split_line, split_acc = run_split(args, torch, psr, dev, b, opts, stream, flush, mean_ms,
+                                          evaluated)
+
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
         cb, err, tg, ref = cpu_baseline(b, acc32, args.cpu_targets, return_ref=True)
+        if split_line:
+            for o in split_line["orders"]:
+                d = split_acc[o["order"]][tg] - ref
+                o["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
         for v in variants:
             d = v["acc"][tg] - ref
             rel = np.linalg.norm(d, axis=1) / np.maximum(np.linalg.norm(ref, axis=1),
@@ -661,6 +762,7 @@ def run_psr(args):
         "batch": batch,
         "pm_long_range": pm_line,
         "fmm_operators": fmm_line,
+        "split_short_range": split_line,
         "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
                         "sampled_targets": None if cb is None else args.cpu_targets},

@@ -127,6 +127,10 @@ typedef struct {
     const int64_t* perm;     /* host, n: sorted index -> original index
                                 (owned by the handle); NULL for a handle built
                                 on the device                                  */
+    int64_t n_far;           /* well-separated (M2L) leaf-pair entries of a
+                                psr_device_build_split handle, else 0; n_pairs
+                                then counts the near (P2P) entries only        */
+    double theta;            /* acceptance parameter of that split, else 0    */
 } psr_info;
 
 typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
@@ -316,7 +320,14 @@ int psr_leaves_host_arrays(const psr_leaves* h, psr_host_arrays* out);
  * the permutation of a device-built handle.  Errors: PSR_E_ARG (NULL).
  */
 typedef struct {
-    size_t pf, pd, perm, leaf, lcen, rowptr, pairs, items, total;
+    size_t pf, pd, perm, leaf, lcen, rowptr, pairs, items;
+    size_t frow, fpairs, fcen, fofs; /* multipole split only: far CSR
+                                  (n_leaves + 1 int64), far entries (n_far
+                                  uint32, the pair list's encoding), expansion
+                                  centres (n_leaves x 4 FP64: x, y, z, radius),
+                                  their offsets from the cell centres lcen
+                                  (n_leaves x 4 FP32: x, y, z, radius)       */
+    size_t total;
 } psr_regions;
 int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
 
@@ -330,7 +341,7 @@ int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
  * size the workspace from the counts:
  *
  * psr_device_build_scratch_bytes - host: scratch bytes psr_device_build
- * needs for n particles (about 320 per particle).  Errors: PSR_E_ARG
+ * needs for n particles (about 360 per particle).  Errors: PSR_E_ARG
  * (n < 1 or n > 2^28, NULL).
  *
  * psr_device_build - enqueue key, radix sort, leaf, radix tree and pair
@@ -366,6 +377,32 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
                      int max_leaf, int flags, void* d_scratch, size_t scratch_bytes,
                      void* cuda_stream, int timeout_ms, psr_leaves** out);
 int psr_device_build_finish(psr_leaves* h, void* d_ws, size_t bytes, void* cuda_stream);
+
+/*
+ * psr_device_build_split - psr_device_build with the multipole split of the
+ * paper's PM-FMM short range (Section 2: cell pairs that are well separated
+ * interact through M2L, the rest through P2P).  Every leaf-pair entry the
+ * walk finds within r_c goes to exactly one of two lists:
+ *   far   the particle boxes' centres are R apart with theta |R| >= rho_I +
+ *         rho_J (rho: half the box diagonal) and every point of one box lies
+ *         within r_c of every point of the other (so the hard cutoff removes
+ *         no pair of the expansion);
+ *   near  every other entry, including i = j.
+ * The handle's pair list (what psr_p2p_forces and psr_p2p_adjoint evaluate)
+ * holds the near entries only; the far list and the expansion centres are
+ * in the workspace (psr_leaves_regions: frow, fpairs, fcen) for
+ * psr_fmm_forces.  The union of the two lists is the list psr_device_build
+ * writes.  theta in (0, 1].  The classification is made in FP32: the
+ * inside test rigorously (boxes rounded outward, distances rounded up,
+ * against r_c^2 (1 - 1e-6) rounded down), the opening test with plain
+ * rounding, so that an entry within about 1e-6 of the opening threshold may
+ * fall on either side.
+ * Errors: those of psr_device_build; PSR_E_ARG for theta outside (0, 1].
+ */
+int psr_device_build_split(const double* d_pos, const double* d_mass, int64_t n,
+                           const psr_box* box, int max_leaf, int flags, double theta,
+                           void* d_scratch, size_t scratch_bytes, void* cuda_stream,
+                           int timeout_ms, psr_leaves** out);
 
 /* ------------------------------------------------- long-range PM part */
 /*
@@ -420,8 +457,10 @@ void psr_pm_free(psr_pm* pm);
  * Cells are CSR ranges [first[c], first[c+1]) of a particle array.
  * Expansions to order p (1 <= p <= 6), multi-indices |n| <= p in graded
  * order (|n|, then n1 descending, then n2 descending), coefficients scaled
- * by a caller-chosen length h (the cell size is a good choice: h^(2k+1)
- * f_(k) then stays within FP32 for well-separated cells):
+ * by a caller-chosen length h so that FP32 holds them (the cell size or r_s
+ * are good choices; each M2L entry forms its derivatives at the scale |R|
+ * and rescales by (h/|R|)^(|k|+1), so any h with (h/|R|)^(p+1) and
+ * (|R|/h)^(p+1) inside the FP32 range works):
  *   Mh_m = sum_j m_j ((z_A - x_j)/h)^m / m!                       (P2M)
  *   Lh_n = sum_{|m| <= p-|n|} Mh_m h^(|n|+|m|+1) D_{n+m}(z_B - z_A) (M2L)
  *   a_c(x) = (G/h^2) sum_{|k| <= p-1} Lh_{k+e_c} ((x - z_B)/h)^k / k!  (L2P)
@@ -441,9 +480,21 @@ void psr_pm_free(psr_pm* pm);
  * psr_fmm_l2p - accelerations of the particles of each cell from its local
  *   coefficients, times box->G; PSR_FMM_ACCUMULATE adds into d_acc (n x 3
  *   FP32) instead of overwriting.
- * Errors: PSR_E_ARG (order, scale, NULL, counts), PSR_E_CUDA.
+ * psr_fmm_forces - the far part of the short range on a psr_device_build_split
+ *   handle (after psr_device_build_finish; the FP64 particle copy must be
+ *   present): P2M on every leaf about its expansion centre, M2L over the
+ *   far list, L2P on every leaf, with h = box r_s.  d_M and d_L: device
+ *   scratch of n_leaves x ncoef4 FP32 each (ncoef rounded up to a multiple
+ *   of 4: the rows load as float4), 16-byte aligned.  d_acc: n x 3 in the ORIGINAL
+ *   particle order (as psr_p2p_forces), FP32, or FP64 with PSR_FMM_F64;
+ *   PSR_FMM_ACCUMULATE adds into it (e.g. onto the near part from
+ *   psr_p2p_forces).  d_status as for psr_fmm_m2l.
+ *   Three launches, asynchronous, graph-capturable.
+ * Errors: PSR_E_ARG (order, scale, NULL, counts, flags), PSR_E_STATE (not a
+ * split handle with its workspace written and its FP64 copy), PSR_E_CUDA.
  */
 #define PSR_FMM_ACCUMULATE 1
+#define PSR_FMM_F64 2
 int psr_fmm_ncoef(int p, int* ncoef);
 int psr_fmm_p2m(int p, double h, int64_t n, int64_t ncell, const int64_t* d_first,
                 const double* d_pos, const double* d_mass, const double* d_centre, float* d_M,
@@ -455,6 +506,8 @@ int psr_fmm_m2l(int p, double h, const psr_box* box, int64_t ntarget, int64_t ns
 int psr_fmm_l2p(int p, double h, const psr_box* box, int64_t ncell, const int64_t* d_first,
                 const double* d_pos, const double* d_centre, const float* d_L, float* d_acc,
                 int flags, void* cuda_stream);
+int psr_fmm_forces(const psr_leaves* h, int p, int flags, float* d_M, float* d_L, void* d_acc,
+                   unsigned* d_status, void* cuda_stream);
 
 /* psr_free_leaves - host: free a handle (NULL is ignored). */
 void psr_free_leaves(psr_leaves* h);

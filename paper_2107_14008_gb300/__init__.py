@@ -125,10 +125,12 @@ class Leaves:
 
     @classmethod
     def device_build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, stream=None,
-                     timeout_ms=60000):
+                     timeout_ms=60000, theta=None):
         """Build on the GPU from device tensors (psr_device_build and
         psr_device_build_finish): pos (n,3) and mass (n,) or None, on one CUDA
-        device.  The result is already resident (no upload())."""
+        device.  The result is already resident (no upload()).  With theta in
+        (0, 1] the pair list is split (psr_device_build_split): forces() then
+        sums the near entries and fmm_forces() the well-separated ones."""
         import torch
         if not (hasattr(pos, "is_cuda") and pos.is_cuda):
             raise ValueError("device_build takes CUDA tensors")
@@ -144,10 +146,16 @@ class Leaves:
             st = _stream_handle(stream)
             nbytes = capi.psr_device_build_scratch_bytes(n)
             scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-            h = capi.psr_device_build(p.data_ptr(), 0 if m is None else m.data_ptr(), n,
-                                      _box(L, r_s, r_c, G), int(max_leaf),
-                                      0 if fp64 else capi.PSR_BUILD_NO_FP64, scratch.data_ptr(),
-                                      nbytes, st, int(timeout_ms))
+            flags = 0 if fp64 else capi.PSR_BUILD_NO_FP64
+            if theta is None:
+                h = capi.psr_device_build(p.data_ptr(), 0 if m is None else m.data_ptr(), n,
+                                          _box(L, r_s, r_c, G), int(max_leaf), flags,
+                                          scratch.data_ptr(), nbytes, st, int(timeout_ms))
+            else:
+                h = capi.psr_device_build_split(p.data_ptr(), 0 if m is None else m.data_ptr(),
+                                                n, _box(L, r_s, r_c, G), int(max_leaf), flags,
+                                                float(theta), scratch.data_ptr(), nbytes, st,
+                                                int(timeout_ms))
             lv = cls(h, n)
             lv.workspace = torch.empty(int(lv._info.device_bytes), dtype=torch.uint8, device=dev)
             capi.psr_device_build_finish(h, lv.workspace.data_ptr(), lv.workspace.numel(), st)
@@ -200,6 +208,26 @@ class Leaves:
         has_pd = n > 0 and r.perm - r.pd >= 32 * n  # the FP64 region is empty without it
         out["pd"] = v(r.pd, 4 * n, torch.float64, (n, 4)) if has_pd else None
         return out
+
+    def far_arrays(self):
+        """Copies (numpy) of the multipole split's workspace arrays: frow
+        (n_leaves+1), fpairs (n_far uint32) and fcen (n_leaves x 4: expansion
+        centre, radius)."""
+        import torch
+        if self.workspace is None or self._info.theta <= 0:
+            raise PsrError(capi.PSR_E_STATE, "not a written split handle")
+        torch.cuda.synchronize(self.workspace.device)
+        r = capi.psr_leaves_regions(self._h)
+        nl, nf = int(self._info.n_leaves), int(self._info.n_far)
+        ws = self.workspace
+
+        def v(off, count, dt, shape):
+            nb = count * torch.empty(0, dtype=dt).element_size()
+            return ws[off:off + nb].view(dt).cpu().numpy().reshape(shape)
+        return {"frow": v(r.frow, nl + 1, torch.int64, (nl + 1,)),
+                "fpairs": v(r.fpairs, nf, torch.int32, (nf,)).view(np.uint32),
+                "fcen": v(r.fcen, 4 * nl, torch.float64, (nl, 4)),
+                "fofs": v(r.fofs, 4 * nl, torch.float32, (nl, 4))}
 
     def host_arrays(self):
         """Copies of the host arrays psr_upload sends (see psr_leaves_host_arrays)."""
@@ -259,6 +287,36 @@ class Leaves:
             raise ValueError("out must be a contiguous (n,3) %s tensor on %s" % (dt, dev))
         with torch.cuda.device(dev):
             capi.psr_p2p_forces(self._h, opts.c(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def fmm_forces(self, p=4, out=None, accumulate=False, fp64=False, scratch=None, status=None,
+                   stream=None):
+        """Far part of the short range of a split handle (psr_fmm_forces):
+        P2M, M2L over the well-separated entries, L2P; (n,3) in the original
+        order, written, or added into `out` with accumulate=True (e.g. onto
+        forces()).  scratch: optional float32 tensor of 2 n_leaves ncoef4
+        elements (ncoef rounded up to a multiple of 4)."""
+        import torch
+        dt = torch.float64 if fp64 else torch.float32
+        dev = self._dev()
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs out")
+            out = torch.empty((self.n, 3), dtype=dt, device=dev)
+        if out.dtype != dt or out.shape != (self.n, 3) or not out.is_contiguous() or out.device != dev:
+            raise ValueError("out must be a contiguous (n,3) %s tensor on %s" % (dt, dev))
+        nc = (capi.psr_fmm_ncoef(p) + 3) // 4 * 4
+        nl = int(self._info.n_leaves)
+        if scratch is None:
+            scratch = torch.empty(2 * max(nl, 1) * nc, dtype=torch.float32, device=dev)
+        if scratch.dtype != torch.float32 or scratch.numel() < 2 * nl * nc or scratch.device != dev:
+            raise ValueError("scratch must be float32 with 2 n_leaves ncoef elements on %s" % dev)
+        flags = (capi.PSR_FMM_ACCUMULATE if accumulate else 0) | (capi.PSR_FMM_F64 if fp64 else 0)
+        with torch.cuda.device(dev):
+            capi.psr_fmm_forces(self._h, p, flags, scratch.data_ptr(),
+                                scratch.data_ptr() + 4 * nl * nc, out.data_ptr(),
+                                0 if status is None else status.data_ptr(),
+                                _stream_handle(stream))
         return out
 
     def adjoint(self, cot, opts=None, grad_pos=None, grad_mass=None, stream=None):

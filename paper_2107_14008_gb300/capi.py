@@ -19,16 +19,17 @@ PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
 PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED = 0, 1, 2
 PSR_BUILD_NO_FP64 = 1
 PSR_PM_ACCUMULATE, PSR_PM_NO_DECONVOLVE = 1, 2
-PSR_FMM_ACCUMULATE = 1
+PSR_FMM_ACCUMULATE, PSR_FMM_F64 = 1, 2
 
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
            "psr_check", "psr_table", "psr_autotune",
            "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
-           "psr_device_build", "psr_device_build_finish", "psr_pm_create", "psr_pm_scratch_bytes",
-           "psr_pm_forces", "psr_pm_free", "psr_fmm_ncoef", "psr_fmm_p2m", "psr_fmm_m2l",
-           "psr_fmm_l2p", "psr_free_leaves", "psr_last_error", "psr_version"]
+           "psr_device_build", "psr_device_build_finish", "psr_device_build_split",
+           "psr_pm_create", "psr_pm_scratch_bytes", "psr_pm_forces", "psr_pm_free",
+           "psr_fmm_ncoef", "psr_fmm_p2m", "psr_fmm_m2l", "psr_fmm_l2p", "psr_fmm_forces",
+           "psr_free_leaves", "psr_last_error", "psr_version"]
 
 
 class psr_box(ctypes.Structure):
@@ -50,7 +51,8 @@ class psr_info(ctypes.Structure):
                 ("n_items", ctypes.c_int64), ("nbox", ctypes.c_int64),
                 ("evaluated_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("max_leaf", ctypes.c_int), ("max_row", ctypes.c_int),
-                ("build_seconds", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64))]
+                ("build_seconds", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
+                ("n_far", ctypes.c_int64), ("theta", ctypes.c_double)]
 
 
 class psr_host_arrays(ctypes.Structure):
@@ -63,7 +65,8 @@ class psr_host_arrays(ctypes.Structure):
 
 class psr_regions(ctypes.Structure):
     _fields_ = [(k, ctypes.c_size_t) for k in
-                ("pf", "pd", "perm", "leaf", "lcen", "rowptr", "pairs", "items", "total")]
+                ("pf", "pd", "perm", "leaf", "lcen", "rowptr", "pairs", "items", "frow", "fpairs",
+                 "fcen", "fofs", "total")]
 
 
 class PsrError(RuntimeError):
@@ -107,6 +110,9 @@ def lib():
                                    ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_int,
                                    ctypes.POINTER(vp)]
     L.psr_device_build_finish.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.psr_device_build_split.argtypes = [vp, vp, i64, ctypes.POINTER(psr_box), ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, vp, ctypes.c_size_t, vp,
+                                         ctypes.c_int, ctypes.POINTER(vp)]
     L.psr_pm_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
     L.psr_pm_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.psr_pm_forces.argtypes = [vp, vp, vp, i64, ctypes.POINTER(psr_box), ctypes.c_int, vp,
@@ -119,6 +125,7 @@ def lib():
                               vp, vp, vp, vp, vp, vp, vp, vp]
     L.psr_fmm_l2p.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(psr_box), i64, vp, vp,
                               vp, vp, vp, ctypes.c_int, vp]
+    L.psr_fmm_forces.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
     L.psr_free_leaves.argtypes = [vp]
     L.psr_free_leaves.restype = None
     L.psr_last_error.restype = ctypes.c_char_p
@@ -231,6 +238,16 @@ def psr_device_build(d_pos, d_mass, n, box, max_leaf, flags, d_scratch, scratch_
     return h
 
 
+def psr_device_build_split(d_pos, d_mass, n, box, max_leaf, flags, theta, d_scratch,
+                           scratch_bytes, stream, timeout_ms):
+    h = ctypes.c_void_p()
+    check(lib().psr_device_build_split(ctypes.c_void_p(d_pos), ctypes.c_void_p(d_mass), n,
+                                       ctypes.byref(box), max_leaf, flags, float(theta),
+                                       ctypes.c_void_p(d_scratch), scratch_bytes,
+                                       ctypes.c_void_p(stream), timeout_ms, ctypes.byref(h)))
+    return h
+
+
 def psr_device_build_finish(h, d_ws, nbytes, stream):
     return check(lib().psr_device_build_finish(h, ctypes.c_void_p(d_ws), nbytes,
                                                ctypes.c_void_p(stream)))
@@ -285,6 +302,11 @@ def psr_fmm_l2p(p, h, box, ncell, d_first, d_pos, d_centre, d_L, d_acc, flags, s
     return check(lib().psr_fmm_l2p(int(p), float(h), ctypes.byref(box), ncell, _vp(d_first),
                                    _vp(d_pos), _vp(d_centre), _vp(d_L), _vp(d_acc), int(flags),
                                    _vp(stream)))
+
+
+def psr_fmm_forces(h, p, flags, d_M, d_L, d_acc, d_status, stream):
+    return check(lib().psr_fmm_forces(h, int(p), int(flags), _vp(d_M), _vp(d_L), _vp(d_acc),
+                                      _vp(d_status), _vp(stream)))
 
 
 def psr_free_leaves(h):

@@ -282,6 +282,10 @@ Layout make_layout(const Leaves& h)
     L.table = o;     o = align256(o + 2 * (size_t)(kMaxTableN + 1) * 16);
     L.cotf = o;      o = align256(o + n * ((h.flags & PSR_BUILD_NO_FP64) ? 16 : 32));
     L.ctrl = o;      o = align256(o + kCtrlWords * 4);
+    L.frow = o;      o = align256(o + (h.has_far ? (nl + 1) * 8 : 0));
+    L.fpairs = o;    o = align256(o + (h.has_far ? (size_t)h.n_far * 4 : 0));
+    L.fcen = o;      o = align256(o + (h.has_far ? nl * 32 : 0));
+    L.fofs = o;      o = align256(o + (h.has_far ? nl * 16 : 0));
     L.total = o;
     return L;
 }

@@ -264,6 +264,8 @@ int psr_leaves_info(const psr_leaves* hh, psr_info* info)
     info->max_row = h->max_row;
     info->build_seconds = h->build_seconds;
     info->perm = h->device_built ? nullptr : h->perm.data();
+    info->n_far = h->n_far;
+    info->theta = h->theta;
     return PSR_OK;
 }
 
@@ -523,6 +525,10 @@ int psr_leaves_regions(const psr_leaves* hh, psr_regions* out)
     out->rowptr = L.rowptr;
     out->pairs = L.pairs;
     out->items = L.items;
+    out->frow = L.frow;
+    out->fpairs = L.fpairs;
+    out->fcen = L.fcen;
+    out->fofs = L.fofs;
     out->total = L.total;
     return PSR_OK;
 }

@@ -61,6 +61,7 @@ enum : int {
     kCntMaxCost = 3,
     kCntMaxRow = 4,
     kCntError = 5,  // bit 0 non-finite input, bit 1 stack overflow, bit 2 malformed tree
+    kCntFar = 6,    // well-separated (M2L) entries of the multipole split
     kCntWords = 8,
 };
 
@@ -69,7 +70,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Scratch regions (byte offsets); leaf arrays are sized for n leaves (max_leaf 1).
 struct Scratch {
     size_t wpos, key0, key1, val0, val1, flag, lid, lfirst, llevel, lkey, lbox, lrec, lcnt,
-        lcost, tnode, tspan, tparl, tpari, tbox, nodef, tflag, hist, tiles, total, cnt, bytes;
+        lfar, lout, lcost, tnode, tspan, tparl, tpari, tbox, nodef, tflag, hist, tiles, total, cnt, bytes;
 };
 
 Scratch scratch_layout(int64_t n)
@@ -94,6 +95,8 @@ Scratch scratch_layout(int64_t n)
     s.lbox = o;   o = a256(o + 48 * N);
     s.lrec = o;   o = a256(o + 32 * N);  // FP32 inward leaf box and count
     s.lcnt = o;   o = a256(o + 8 * N);
+    s.lfar = o;   o = a256(o + 8 * N);   // far entries per leaf (multipole split)
+    s.lout = o;   o = a256(o + 32 * N);  // FP32 leaf box rounded outward (multipole split)
     s.lcost = o;  o = a256(o + 8 * N);
     s.tnode = o;  o = a256(o + 8 * N);
     s.tspan = o;  o = a256(o + 8 * N);   // leaf range [lo, hi] of each internal node
@@ -113,6 +116,8 @@ Scratch scratch_layout(int64_t n)
 struct BoxK {
     double L, scale, unit, inv2rs, rc2m;  // rc2m = r_c^2 (1 + 1e-5), the host's margin
     float thi, tlo;  // FP32 thresholds: thi >= rc2m (1 + 1e-6), tlo <= rc2m (1 - 1e-6)
+    float theta2;    // multipole split: theta^2 (0: no split)
+    float rc2far;    // FP32 at most r_c^2 (1 - 1e-6): a far pair lies wholly inside the cutoff
 };
 
 // ------------------------------------------------------------ utilities --
@@ -474,7 +479,7 @@ __global__ void k_leaf_fill(const int64_t* __restrict__ flag, const int64_t* __r
 __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64_t n,
                            const double* __restrict__ wpos, const int32_t* __restrict__ idx,
                            double* __restrict__ lbox, float4* __restrict__ lrec,
-                           long long* __restrict__ cnt)
+                           float4* __restrict__ lout, long long* __restrict__ cnt)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= nl) return;
@@ -497,6 +502,11 @@ __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64
                               __double2float_ru(lo[2]), __int_as_float((int)(e - f)));
     lrec[2 * g + 1] = make_float4(__double2float_rd(hi[0]), __double2float_rd(hi[1]),
                                   __double2float_rd(hi[2]), 0.f);
+    // the box rounded outward (lo down, hi up), for the multipole split
+    lout[2 * g] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
+                              __double2float_rd(lo[2]), 0.f);
+    lout[2 * g + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
+                                  __double2float_ru(hi[2]), 0.f);
     atomicMax(cnt + kCntMaxLeaf, (long long)(e - f));
 }
 
@@ -671,6 +681,38 @@ __device__ __forceinline__ float maxgap2_upper(const float* alo, const float* ah
     return s;
 }
 
+// The multipole split: leaf J + shift is well separated from leaf I when
+// every point of one box lies within r_c of every point of the other (a
+// rigorous FP32 upper bound of the largest point-pair distance, from boxes
+// rounded outward, against r_c^2 (1 - 1e-6) rounded down: the cutoff then
+// removes no pair the expansion includes) and the box centres are R apart
+// with theta |R| >= rho_I + rho_J (rho: half the box diagonal; an opening
+// test, in FP32 with explicit roundings so that the count and the write
+// pass decide alike).  alo/ahi: box I rounded outward; b0/b1: box J
+// rounded outward (lo.xyz, hi.xyz).
+__device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, float4 b0, float4 b1,
+                                         const float* sd, const float* su, float theta2,
+                                         float rc2far)
+{
+    const float blo[3] = {b0.x, b0.y, b0.z}, bhi[3] = {b1.x, b1.y, b1.z};
+    float m2 = 0.f, d2 = 0.f, ra2 = 0.f, rb2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float bl = __fadd_rd(blo[a], sd[a]), bh = __fadd_ru(bhi[a], su[a]);
+        const float mx = fmaxf(__fsub_ru(bh, alo[a]), __fsub_ru(ahi[a], bl));
+        m2 = __fmaf_ru(mx, mx, m2);
+        const float d = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(bl, bh)),
+                                  __fmul_rn(0.5f, __fadd_rn(alo[a], ahi[a])));
+        const float ea = __fmul_rn(0.5f, __fsub_rn(ahi[a], alo[a]));
+        const float eb = __fmul_rn(0.5f, __fsub_rn(bh, bl));
+        d2 = __fmaf_rn(d, d, d2);
+        ra2 = __fmaf_rn(ea, ea, ra2);
+        rb2 = __fmaf_rn(eb, eb, rb2);
+    }
+    const float r = __fadd_rn(__fsqrt_rn(ra2), __fsqrt_rn(rb2));
+    return d2 > 0.f && m2 < rc2far && __fmul_rn(theta2, d2) >= __fmul_rn(r, r);
+}
+
 // One thread per target leaf.  WRITE = false counts the row and its work;
 // WRITE = true writes the row at rowptr.  Nodes are pruned when the FP32
 // lower bound of their gap^2 reaches thi (then the host's FP64 test fails
@@ -684,9 +726,11 @@ template <bool WRITE>
 __global__ void __launch_bounds__(128, 8) k_pairs(
     int64_t nl, int64_t n, BoxK bx, const int32_t* __restrict__ lfirst,
     const double* __restrict__ lbox, const float4* __restrict__ lrec,
+    const float4* __restrict__ lout,
     const float4* __restrict__ nodef, const double* __restrict__ rootbox,
     int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
-    uint32_t* __restrict__ pairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
+    uint32_t* __restrict__ pairs, int64_t* __restrict__ lfar, const int64_t* __restrict__ frowptr,
+    uint32_t* __restrict__ fpairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
 {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= nl) return;
@@ -704,27 +748,62 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
     }
     // stack entries: (node code, -1) or a leaf range (first, last) kept whole
     int2 stack[kStackDepth];
-    int64_t c = 0, src = 0;
+    int64_t c = 0, src = 0, cf = 0;
     int64_t w = WRITE ? rowptr[I] : 0;
     const int64_t wend = WRITE ? rowptr[I + 1] : 0;
+    const bool split = bx.theta2 > 0.0f;
+    int64_t fw = (WRITE && split) ? frowptr[I] : 0;
+    const int64_t fwend = (WRITE && split) ? frowptr[I + 1] : 0;
     bool bad = false;
-    // keeps leaves [f, l] of this image
+    double sh[3];
+    float sd[3], su[3];  // the shift rounded down and up
+    // keeps leaves [f, l] of this image: all into the pair list, or, with the
+    // multipole split, each into the far list or the pair list
     auto take = [&](int f, int l, int code) {
-        c += l - f + 1;
-        src += lfirst[l + 1] - lfirst[f];
-        if (WRITE) {
-            if (w + (l - f + 1) > wend) {
-                atomicOr(err, 4u);
-                bad = true;
-                return;
+        if (!split) {
+            c += l - f + 1;
+            src += lfirst[l + 1] - lfirst[f];
+            if (WRITE) {
+                if (w + (l - f + 1) > wend) {
+                    atomicOr(err, 4u);
+                    bad = true;
+                    return;
+                }
+                for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
             }
-            for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
+            return;
+        }
+        for (int J = f; J <= l; ++J) {
+            const uint32_t ent = ((uint32_t)J << 5) | (uint32_t)code;
+            if (far_pair(aolo, aohi, lout[2 * (int64_t)J], lout[2 * (int64_t)J + 1], sd, su,
+                         bx.theta2, bx.rc2far)) {
+                ++cf;
+                if (WRITE) {
+                    if (fw >= fwend) {
+                        atomicOr(err, 4u);
+                        bad = true;
+                        return;
+                    }
+                    fpairs[fw++] = ent;
+                }
+            } else {
+                ++c;
+                src += lfirst[J + 1] - lfirst[J];
+                if (WRITE) {
+                    if (w >= wend) {
+                        atomicOr(err, 4u);
+                        bad = true;
+                        return;
+                    }
+                    pairs[w++] = ent;
+                }
+            }
         }
     };
     for (int code = 0; code < kShiftCodes && !bad; ++code) {
-        const double sh[3] = {(code / 9 - 1) * bx.L, ((code / 3) % 3 - 1) * bx.L,
-                              (code % 3 - 1) * bx.L};
-        float sd[3], su[3];
+        sh[0] = (code / 9 - 1) * bx.L;
+        sh[1] = ((code / 3) % 3 - 1) * bx.L;
+        sh[2] = (code % 3 - 1) * bx.L;
         for (int a = 0; a < 3; ++a) {
             sd[a] = __double2float_rd(sh[a]);
             su[a] = __double2float_ru(sh[a]);
@@ -792,16 +871,45 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
             }
         }
     }
-    if (WRITE && !bad && w != wend) atomicOr(err, 4u);
+    if (WRITE && !bad && (w != wend || fw != fwend)) atomicOr(err, 4u);
     if (!WRITE) {
         const int64_t nI = lfirst[I + 1] - lfirst[I];
         lcnt[I] = c;
+        if (split) {
+            lfar[I] = cf;
+            atomicAdd((unsigned long long*)(cnt + kCntFar), (unsigned long long)cf);
+        }
         lcost[I] = src * nI;
         atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
         atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
         atomicMax(cnt + kCntMaxCost, (long long)(src * nI));
         atomicMax(cnt + kCntMaxRow, (long long)c);
     }
+}
+
+// Expansion centre and radius of each leaf for the multipole split: the
+// centre of its particle box and half the box diagonal; also the centre's
+// offset from the leaf's cell centre (lcen, units of L / 2^22) in FP32, so
+// that centre differences are an exact integer part plus a small FP32 one.
+__global__ void k_fcen(const double* __restrict__ lbox, const int4* __restrict__ lcen,
+                       double unit, int64_t nl, double4* __restrict__ fcen,
+                       float4* __restrict__ fofs)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    const double* A = lbox + 6 * g;
+    const int4 q = lcen[g];
+    const int qc[3] = {q.x, q.y, q.z};
+    double c[3], o[3], r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double ea = __dmul_rn(0.5, __dsub_rn(A[3 + a], A[a]));
+        c[a] = __dmul_rn(0.5, __dadd_rn(A[a], A[3 + a]));
+        o[a] = __dsub_rn(c[a], __dmul_rn((double)qc[a], unit));
+        r2 = __dadd_rn(r2, __dmul_rn(ea, ea));
+    }
+    const double r = __dsqrt_rn(r2);
+    fcen[g] = make_double4(c[0], c[1], c[2], r);
+    fofs[g] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)r);
 }
 
 // --------------------------------------------------------------- payload --
@@ -904,6 +1012,8 @@ BoxK box_k(const psr_box& b)
     k.rc2m = b.r_c * b.r_c * (1.0 + 1e-5);
     k.thi = float_at_least(k.rc2m * (1.0 + 1e-6));
     k.tlo = float_at_most(k.rc2m * (1.0 - 1e-6));
+    k.theta2 = 0.0f;
+    k.rc2far = float_at_most(b.r_c * b.r_c * (1.0 - 1e-6));
     return k;
 }
 
@@ -922,9 +1032,13 @@ int psr_device_build_scratch_bytes(int64_t n, size_t* bytes)
     return PSR_OK;
 }
 
-int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const psr_box* box,
-                     int max_leaf, int flags, void* d_scratch, size_t scratch_bytes, void* stream,
-                     int timeout_ms, psr_leaves** out)
+}  // extern "C"
+
+namespace {
+
+int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr_box* box,
+                 int max_leaf, int flags, double theta, void* d_scratch, size_t scratch_bytes,
+                 void* stream, int timeout_ms, psr_leaves** out)
 {
     auto t0 = std::chrono::steady_clock::now();
     if (!out) return dfail(PSR_E_ARG, "null output");
@@ -970,7 +1084,8 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
     int64_t* tiles = (int64_t*)(s + S.tiles);
     int64_t* total = (int64_t*)(s + S.total);
     long long* cnt = (long long*)(s + S.cnt);
-    const BoxK bx = box_k(*box);
+    BoxK bx = box_k(*box);
+    bx.theta2 = (float)(theta * theta);
 
     int e;
     if ((e = (int)cudaMemsetAsync(cnt, 0, 8 * kCntWords, st))) return dcuda(e, "cudaMemsetAsync");
@@ -989,7 +1104,8 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 1) return dfail(PSR_E_ARG, "non-finite position or mass");
     if (nl < 1 || nl > n || nl >= (1 << 27)) return dfail(PSR_E_ARG, "leaf count out of range");
-    k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, lrec, cnt);
+    k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, lrec,
+                                              (float4*)(s + S.lout), cnt);
     if (nl >= 2) {
         if ((e = (int)cudaMemsetAsync(tflag, 0, 4 * (nl - 1), st))) return dcuda(e, "cudaMemsetAsync");
         k_tree_nodes<<<nblk(nl - 1, 256), 256, 0, st>>>(lkey, nl, tnode, tspan, tparl, tpari);
@@ -997,14 +1113,17 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
         k_tree_pack<<<nblk(nl - 1, 256), 256, 0, st>>>(nl, tnode, tspan, lbox, tbox, nodef);
     }
     const double* rootbox = nl >= 2 ? tbox : lbox;
-    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec, nodef, rootbox,
-                                                  lcnt, lcost, nullptr, nullptr, cnt,
+    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec,
+                                                  (const float4*)(s + S.lout), nodef, rootbox,
+                                                  lcnt, lcost, nullptr, nullptr,
+                                                  (int64_t*)(s + S.lfar), nullptr, nullptr, cnt,
                                                   (unsigned*)(cnt + kCntError));
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair count kernel");
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 2) return dfail(PSR_E_DEVICE, "tree traversal stack overflow");
     if (c[kCntError] & 4) return dfail(PSR_E_DEVICE, "malformed radix tree");
-    if (c[kCntPairs] >= ((int64_t)1 << 32)) return dfail(PSR_E_ARG, "more than 2^32 leaf pairs");
+    if (c[kCntPairs] >= ((int64_t)1 << 32) || c[kCntFar] >= ((int64_t)1 << 32))
+        return dfail(PSR_E_ARG, "more than 2^32 leaf pairs");
 
     Leaves* h = new (std::nothrow) Leaves();
     if (!h) return dfail(PSR_E_NOMEM, "out of host memory");
@@ -1022,6 +1141,9 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
         h->max_row = (int)c[kCntMaxRow];
         h->has_pd = !(flags & PSR_BUILD_NO_FP64);
         h->device_built = true;
+        h->has_far = theta > 0.0;
+        h->theta = theta;
+        h->n_far = theta > 0.0 ? c[kCntFar] : 0;
         h->boxdev = {box_constants(*box)};
         h->lay = make_layout(*h);
     } catch (const std::bad_alloc&) {
@@ -1033,6 +1155,29 @@ int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = reinterpret_cast<psr_leaves*>(h);
     return PSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psr_device_build(const double* d_pos, const double* d_mass, int64_t n, const psr_box* box,
+                     int max_leaf, int flags, void* d_scratch, size_t scratch_bytes, void* stream,
+                     int timeout_ms, psr_leaves** out)
+{
+    return device_build(d_pos, d_mass, n, box, max_leaf, flags, 0.0, d_scratch, scratch_bytes,
+                        stream, timeout_ms, out);
+}
+
+int psr_device_build_split(const double* d_pos, const double* d_mass, int64_t n,
+                           const psr_box* box, int max_leaf, int flags, double theta,
+                           void* d_scratch, size_t scratch_bytes, void* stream, int timeout_ms,
+                           psr_leaves** out)
+{
+    if (out) *out = nullptr;
+    if (!(theta > 0.0 && theta <= 1.0)) return dfail(PSR_E_ARG, "theta must be in (0, 1]");
+    return device_build(d_pos, d_mass, n, box, max_leaf, flags, theta, d_scratch, scratch_bytes,
+                        stream, timeout_ms, out);
 }
 
 int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stream)
@@ -1071,10 +1216,23 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
         return dcuda(e, "scan");
     k_copy_total<<<1, 1, 0, st>>>(rowptr + nl, total);
     const double* lbox = (const double*)(s + S.lbox);
+    int64_t* frow = h->has_far ? (int64_t*)(w + L.frow) : nullptr;
+    if (h->has_far) {
+        if ((e = scan_exclusive((const int64_t*)(s + S.lfar), frow, nl, tiles, total, st)))
+            return dcuda(e, "scan");
+        k_copy_total<<<1, 1, 0, st>>>(frow + nl, total);
+        k_fcen<<<nblk(nl, 128), 128, 0, st>>>(lbox, (const int4*)(w + L.lcen), bx.unit, nl,
+                                              (double4*)(w + L.fcen), (float4*)(w + L.fofs));
+        if ((e = (int)cudaGetLastError())) return dcuda(e, "expansion centre kernel");
+    }
+    BoxK bxw = bx;
+    bxw.theta2 = (float)(h->theta * h->theta);
     k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
-        nl, n, bx, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.nodef),
+        nl, n, bxw, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.lout),
+        (const float4*)(s + S.nodef),
         nl >= 2 ? (const double*)(s + S.tbox) : lbox, nullptr, nullptr, rowptr,
-        (uint32_t*)(w + L.pairs), nullptr, (unsigned*)(w + L.ctrl) + kCtrlError);
+        (uint32_t*)(w + L.pairs), nullptr, frow, h->has_far ? (uint32_t*)(w + L.fpairs) : nullptr,
+        nullptr, (unsigned*)(w + L.ctrl) + kCtrlError);
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair write kernel");
     // schedule: the particle sort buffers are free again (values in int32
     // views of the flag / lid regions, both >= 4 nl bytes)

@@ -52,6 +52,11 @@ struct Layout {
     size_t table;    // float4[2 * (kMaxTableN + 1)]: T table, then exp(-x^2)
     size_t cotf;     // float4[n] / double4[n] adjoint source payload scratch
     size_t ctrl;     // uint32[64]  scheduler tickets, error word, counters
+    // multipole split (device builds with an acceptance parameter only)
+    size_t frow;     // int64[nl+1]  CSR of well-separated (M2L) entries by target leaf
+    size_t fpairs;   // uint32[nf]   (source leaf << 5) | shift code
+    size_t fcen;     // double4[nl]  expansion centre (particle box centre), radius
+    size_t fofs;     // float4[nl]   that centre minus the cell centre (lcen), radius
     size_t total;
 };
 
@@ -101,6 +106,9 @@ struct Leaves {
     int64_t n_pairs = 0;
     bool has_pd = false;        // FP64 payload present in the workspace
     bool device_built = false;  // arrays were built on the device
+    bool has_far = false;       // pair list split into P2P (near) and M2L (far) entries
+    double theta = 0.0;         //   multipole acceptance parameter of that split
+    int64_t n_far = 0;          //   far entries
     char* db_scratch = nullptr; // device build between its two calls: the caller's scratch
     int64_t db_maxcost = 0;     //   and the largest per-leaf cost (schedule sort width)
     // device state

@@ -39,6 +39,9 @@ def test_coefficient_counts_and_host_side_checks():
     with pytest.raises(capi.PsrError):
         capi.psr_fmm_m2l(3, 1.0, capi.psr_box(10.0, 0.0, 2.25, 1.0), 2, 2, fake, fake, fake,
                          fake, fake, fake, 0, 0)
+    with pytest.raises(capi.PsrError) as e:  # no handle
+        capi.psr_fmm_forces(None, 4, 0, fake, fake, fake, 0, 0)
+    assert e.value.code == capi.PSR_E_ARG
 
 
 def _scale_M(M, p, h):
@@ -215,3 +218,61 @@ def test_m2l_status_bits_and_skipped_entries():
         out.append((Lg.cpu().numpy(), int(st.item())))
     assert out[0][1] == 0 and out[1][1] == 3  # out of range, then coincident centres
     assert np.array_equal(out[0][0], out[1][0])  # bad entries skipped, the good one kept
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h", [1.0, 300.0, 0.003])
+def test_chain_on_tiny_close_cells_for_any_scale(h):
+    """Cells 4e-3 across, 0.05 apart, order 6: at h = 300 the prefactor
+    h^13 f_(6)(|R|) alone is far outside FP32; each entry forms its
+    derivatives at the scale |R| and rescales, so every h gives the oracle's
+    chain."""
+    rng = np.random.default_rng(21)
+    r_s, G, L, p = 0.7, 1.3, 50.0, 6
+    cs, spos, smass, sfirst = _cells(rng, 1, 25, 2e-3, 0.0)
+    cs += 10.0
+    spos += 10.0
+    ct = cs + np.array([[0.03, -0.035, 0.02]])
+    tpos = ct[0] + rng.uniform(-2e-3, 2e-3, (20, 3))
+    tfirst = np.array([0, 20], np.int64)
+    rowptr, pairs = np.array([0, 1], np.int64), np.array([13], np.uint32)
+    got = _gpu_chain(p, h, r_s, G, L, (cs, spos, smass, sfirst), (ct, tpos, tfirst), rowptr, pairs)
+    Lo = ofmm.m2l(ofmm.p2m(spos, smass, cs[0], p), ct[0] - cs[0], r_s, p)
+    ref = ofmm.l2p(Lo, ct[0], tpos, p, G)
+    assert np.all(np.isfinite(got))
+    assert np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2)) < 1e-4
+
+
+@pytest.mark.gpu
+def test_m2l_ragged_rows_across_lane_groups():
+    """Rows of 0 .. 40 entries for 37 targets (not a multiple of the targets
+    a warp serves), every entry a well-separated pair inside the cutoff."""
+    import torch
+    rng = np.random.default_rng(22)
+    h, r_s, L, p = 1.0, 8.0, 64.0, 4
+    cs, spos, smass, sfirst = _cells(rng, 50, 6, 0.5 * h, L)
+    ct = rng.uniform(0, L, (37, 3))
+    rowptr, pairs = [0], []
+    for t in range(len(ct)):
+        cand = [s for s in rng.permutation(len(cs))
+                if 2.5 * h < np.linalg.norm(ct[t] - cs[s]) < 4.5 * r_s]
+        pairs += [(int(s) << 5) | 13 for s in cand[:(t * 7) % 41]]
+        rowptr.append(len(pairs))
+    rowptr, pairs = np.array(rowptr, np.int64), np.array(pairs, np.uint32)
+    Ms_raw = [ofmm.p2m(spos[sfirst[s]:sfirst[s + 1]], smass[sfirst[s]:sfirst[s + 1]], cs[s], p)
+              for s in range(len(cs))]
+    ref = np.array([_scale_L(l, p, h) for l in _oracle_L(p, r_s, ct, cs, L, rowptr, pairs, Ms_raw)])
+    M = _dev(np.array([_scale_M(m, p, h) for m in Ms_raw]), torch.float32)
+    Lg = torch.full((len(ct), capi.psr_fmm_ncoef(p)), 5.0, dtype=torch.float32, device="cuda")
+    rp, pr = _dev(rowptr, torch.int64), _dev(pairs.view(np.int32), torch.int32)
+    ctd, csd = _dev(ct, torch.float64), _dev(cs, torch.float64)
+    capi.psr_fmm_m2l(p, h, capi.psr_box(L, r_s, 4.5 * r_s, 1.0), len(ct), len(cs), rp.data_ptr(),
+                     pr.data_ptr(), ctd.data_ptr(), csd.data_ptr(), M.data_ptr(), Lg.data_ptr(), 0,
+                     _stream())
+    got = Lg.double().cpu().numpy()
+    for t in range(len(ct)):
+        if rowptr[t + 1] == rowptr[t]:
+            assert np.all(got[t] == 0.0), t
+        else:
+            err = np.sqrt(np.sum((got[t] - ref[t]) ** 2) / np.sum(ref[t] ** 2))
+            assert err < 1e-4, (t, err)
