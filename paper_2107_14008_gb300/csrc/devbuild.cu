@@ -502,11 +502,19 @@ __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64
                               __double2float_ru(lo[2]), __int_as_float((int)(e - f)));
     lrec[2 * g + 1] = make_float4(__double2float_rd(hi[0]), __double2float_rd(hi[1]),
                                   __double2float_rd(hi[2]), 0.f);
-    // the box rounded outward (lo down, hi up), for the multipole split
-    lout[2 * g] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
-                              __double2float_rd(lo[2]), 0.f);
-    lout[2 * g + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
-                                  __double2float_ru(hi[2]), 0.f);
+    // the box rounded outward (lo down, hi up) and half its diagonal, for
+    // the multipole split
+    const float ol[3] = {__double2float_rd(lo[0]), __double2float_rd(lo[1]),
+                         __double2float_rd(lo[2])};
+    const float oh[3] = {__double2float_ru(hi[0]), __double2float_ru(hi[1]),
+                         __double2float_ru(hi[2])};
+    float r2 = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        const float ea = __fmul_rn(0.5f, __fsub_rn(oh[a], ol[a]));
+        r2 = __fmaf_rn(ea, ea, r2);
+    }
+    lout[2 * g] = make_float4(ol[0], ol[1], ol[2], 0.f);
+    lout[2 * g + 1] = make_float4(oh[0], oh[1], oh[2], __fsqrt_rn(r2));
     atomicMax(cnt + kCntMaxLeaf, (long long)(e - f));
 }
 
@@ -686,16 +694,17 @@ __device__ __forceinline__ float maxgap2_upper(const float* alo, const float* ah
 // rigorous FP32 upper bound of the largest point-pair distance, from boxes
 // rounded outward, against r_c^2 (1 - 1e-6) rounded down: the cutoff then
 // removes no pair the expansion includes) and the box centres are R apart
-// with theta |R| >= rho_I + rho_J (rho: half the box diagonal; an opening
-// test, in FP32 with explicit roundings so that the count and the write
-// pass decide alike).  alo/ahi: box I rounded outward; b0/b1: box J
-// rounded outward (lo.xyz, hi.xyz).
-__device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, float4 b0, float4 b1,
-                                         const float* sd, const float* su, float theta2,
-                                         float rc2far)
+// with theta |R| >= rho_I + rho_J (rho: half the diagonal of the outward
+// box; an opening test, in FP32 with explicit roundings so that the count
+// and the write pass decide alike).  alo/ahi, ra: box I and its rho; b0 =
+// (lo of box J), b1 = (hi of box J, rho_J); sd/su: the shift rounded down
+// and up.
+__device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, float ra, float4 b0,
+                                         float4 b1, const float* sd, const float* su,
+                                         float theta2, float rc2far)
 {
     const float blo[3] = {b0.x, b0.y, b0.z}, bhi[3] = {b1.x, b1.y, b1.z};
-    float m2 = 0.f, d2 = 0.f, ra2 = 0.f, rb2 = 0.f;
+    float m2 = 0.f, d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float bl = __fadd_rd(blo[a], sd[a]), bh = __fadd_ru(bhi[a], su[a]);
@@ -703,13 +712,9 @@ __device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, flo
         m2 = __fmaf_ru(mx, mx, m2);
         const float d = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(bl, bh)),
                                   __fmul_rn(0.5f, __fadd_rn(alo[a], ahi[a])));
-        const float ea = __fmul_rn(0.5f, __fsub_rn(ahi[a], alo[a]));
-        const float eb = __fmul_rn(0.5f, __fsub_rn(bh, bl));
         d2 = __fmaf_rn(d, d, d2);
-        ra2 = __fmaf_rn(ea, ea, ra2);
-        rb2 = __fmaf_rn(eb, eb, rb2);
     }
-    const float r = __fadd_rn(__fsqrt_rn(ra2), __fsqrt_rn(rb2));
+    const float r = __fadd_rn(ra, b1.w);
     return d2 > 0.f && m2 < rc2far && __fmul_rn(theta2, d2) >= __fmul_rn(r, r);
 }
 
@@ -726,11 +731,9 @@ template <bool WRITE>
 __global__ void __launch_bounds__(128, 8) k_pairs(
     int64_t nl, int64_t n, BoxK bx, const int32_t* __restrict__ lfirst,
     const double* __restrict__ lbox, const float4* __restrict__ lrec,
-    const float4* __restrict__ lout,
     const float4* __restrict__ nodef, const double* __restrict__ rootbox,
     int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
-    uint32_t* __restrict__ pairs, int64_t* __restrict__ lfar, const int64_t* __restrict__ frowptr,
-    uint32_t* __restrict__ fpairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
+    uint32_t* __restrict__ pairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
 {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= nl) return;
@@ -748,62 +751,27 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
     }
     // stack entries: (node code, -1) or a leaf range (first, last) kept whole
     int2 stack[kStackDepth];
-    int64_t c = 0, src = 0, cf = 0;
+    int64_t c = 0, src = 0;
     int64_t w = WRITE ? rowptr[I] : 0;
     const int64_t wend = WRITE ? rowptr[I + 1] : 0;
-    const bool split = bx.theta2 > 0.0f;
-    int64_t fw = (WRITE && split) ? frowptr[I] : 0;
-    const int64_t fwend = (WRITE && split) ? frowptr[I + 1] : 0;
     bool bad = false;
-    double sh[3];
-    float sd[3], su[3];  // the shift rounded down and up
-    // keeps leaves [f, l] of this image: all into the pair list, or, with the
-    // multipole split, each into the far list or the pair list
+    // keeps leaves [f, l] of this image
     auto take = [&](int f, int l, int code) {
-        if (!split) {
-            c += l - f + 1;
-            src += lfirst[l + 1] - lfirst[f];
-            if (WRITE) {
-                if (w + (l - f + 1) > wend) {
-                    atomicOr(err, 4u);
-                    bad = true;
-                    return;
-                }
-                for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
+        c += l - f + 1;
+        src += lfirst[l + 1] - lfirst[f];
+        if (WRITE) {
+            if (w + (l - f + 1) > wend) {
+                atomicOr(err, 4u);
+                bad = true;
+                return;
             }
-            return;
-        }
-        for (int J = f; J <= l; ++J) {
-            const uint32_t ent = ((uint32_t)J << 5) | (uint32_t)code;
-            if (far_pair(aolo, aohi, lout[2 * (int64_t)J], lout[2 * (int64_t)J + 1], sd, su,
-                         bx.theta2, bx.rc2far)) {
-                ++cf;
-                if (WRITE) {
-                    if (fw >= fwend) {
-                        atomicOr(err, 4u);
-                        bad = true;
-                        return;
-                    }
-                    fpairs[fw++] = ent;
-                }
-            } else {
-                ++c;
-                src += lfirst[J + 1] - lfirst[J];
-                if (WRITE) {
-                    if (w >= wend) {
-                        atomicOr(err, 4u);
-                        bad = true;
-                        return;
-                    }
-                    pairs[w++] = ent;
-                }
-            }
+            for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
         }
     };
     for (int code = 0; code < kShiftCodes && !bad; ++code) {
-        sh[0] = (code / 9 - 1) * bx.L;
-        sh[1] = ((code / 3) % 3 - 1) * bx.L;
-        sh[2] = (code % 3 - 1) * bx.L;
+        const double sh[3] = {(code / 9 - 1) * bx.L, ((code / 3) % 3 - 1) * bx.L,
+                              (code % 3 - 1) * bx.L};
+        float sd[3], su[3];
         for (int a = 0; a < 3; ++a) {
             sd[a] = __double2float_rd(sh[a]);
             su[a] = __double2float_ru(sh[a]);
@@ -871,16 +839,254 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
             }
         }
     }
-    if (WRITE && !bad && (w != wend || fw != fwend)) atomicOr(err, 4u);
+    if (WRITE && !bad && w != wend) atomicOr(err, 4u);
     if (!WRITE) {
         const int64_t nI = lfirst[I + 1] - lfirst[I];
         lcnt[I] = c;
-        if (split) {
-            lfar[I] = cf;
-            atomicAdd((unsigned long long*)(cnt + kCntFar), (unsigned long long)cf);
-        }
         lcost[I] = src * nI;
         atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
+        atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
+        atomicMax(cnt + kCntMaxCost, (long long)(src * nI));
+        atomicMax(cnt + kCntMaxRow, (long long)c);
+    }
+}
+
+// The walk of k_pairs with the multipole split.  A lane's walk does not
+// classify the leaves it keeps: it queues the kept ranges (first, last,
+// image) in shared memory, and whenever a lane's queue is nearly full, or
+// every lane's walk has ended, the warp classifies all queued ranges of all
+// its lanes as one list, 32 source leaves per step (far_pair then runs with
+// every lane busy, where inside a divergent walk it ran one lane at a time),
+// and counts or writes the near and far entries of each owning row in walk
+// order.  Every lane runs the same number of flushes (lanes past the last
+// leaf have ended from the start), so the warp-wide steps see all 32 lanes.
+constexpr int kSplitQ = 8;  // queued ranges per lane (a walk step queues at most 2)
+
+template <bool WRITE>
+__global__ void __launch_bounds__(128, 4) k_pairs_split(
+    int64_t nl, BoxK bx, const int32_t* __restrict__ lfirst, const double* __restrict__ lbox,
+    const float4* __restrict__ lrec, const float4* __restrict__ lout,
+    const float4* __restrict__ nodef, const double* __restrict__ rootbox,
+    int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, int64_t* __restrict__ lfar,
+    const int64_t* __restrict__ rowptr, uint32_t* __restrict__ pairs,
+    const int64_t* __restrict__ frowptr, uint32_t* __restrict__ fpairs,
+    long long* __restrict__ cnt, unsigned* __restrict__ err)
+{
+    constexpr int kQ = kSplitQ, kSlots = 32 * kSplitQ, kWarps = 4;
+    __shared__ int4 sq[kWarps][kSlots];            // (first, last, image, owning lane)
+    __shared__ long long spre[kWarps][kSlots];     // leaves queued before each slot
+    __shared__ float4 sbox[kWarps][32][2];         // owning lane's box rounded outward, rho
+    __shared__ long long sw[kWarps][32], sfw[kWarps][32];    // write positions
+    __shared__ long long swe[kWarps][32], sfwe[kWarps][32];  // row ends
+    __shared__ long long sc[kWarps][32], scf[kWarps][32], ssrc[kWarps][32];  // counts
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool live = I < nl;
+    double A[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float aolo[3] = {0.f, 0.f, 0.f}, aohi[3] = {0.f, 0.f, 0.f};
+    float ailo[3] = {0.f, 0.f, 0.f}, aihi[3] = {0.f, 0.f, 0.f};
+    float rlo[3] = {0.f, 0.f, 0.f}, rhi[3] = {0.f, 0.f, 0.f};
+    sbox[wp][lane][0] = sbox[wp][lane][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    sw[wp][lane] = sfw[wp][lane] = swe[wp][lane] = sfwe[wp][lane] = 0;
+    sc[wp][lane] = scf[wp][lane] = ssrc[wp][lane] = 0;
+    if (live) {
+        for (int a = 0; a < 3; ++a) {
+            A[a] = lbox[6 * I + a];
+            A[3 + a] = lbox[6 * I + 3 + a];
+            aolo[a] = __double2float_rd(A[a]);
+            aohi[a] = __double2float_ru(A[3 + a]);
+            ailo[a] = __double2float_ru(A[a]);
+            aihi[a] = __double2float_rd(A[3 + a]);
+            rlo[a] = __double2float_rd(rootbox[a]);
+            rhi[a] = __double2float_ru(rootbox[3 + a]);
+        }
+        sbox[wp][lane][0] = lout[2 * I];
+        sbox[wp][lane][1] = lout[2 * I + 1];
+        if (WRITE) {
+            sw[wp][lane] = rowptr[I];
+            swe[wp][lane] = rowptr[I + 1];
+            sfw[wp][lane] = frowptr[I];
+            sfwe[wp][lane] = frowptr[I + 1];
+        }
+    }
+    __syncwarp();
+    const float Lrd = __double2float_rd(bx.L), Lru = __double2float_ru(bx.L);
+    int2 stack[kStackDepth];
+    bool bad = false, done = !live, in_tree = false;
+    int code = -1, sp = 0;
+    int2 cur = make_int2(0, -1);
+    int64_t visits = 0;
+    float sd[3] = {0.f, 0.f, 0.f}, su[3] = {0.f, 0.f, 0.f};
+    double sh[3] = {0.0, 0.0, 0.0};
+    int4* myq = &sq[wp][lane * kQ];
+    for (;;) {
+        // ---- walk until the queue may not take another step's ranges
+        int nq = 0;
+        while (!done && nq <= kQ - 2) {
+            if (!in_tree) {
+                if (++code >= kShiftCodes) {
+                    done = true;
+                    break;
+                }
+                sh[0] = (code / 9 - 1) * bx.L;
+                sh[1] = ((code / 3) % 3 - 1) * bx.L;
+                sh[2] = (code % 3 - 1) * bx.L;
+                for (int a = 0; a < 3; ++a) {
+                    sd[a] = __double2float_rd(sh[a]);
+                    su[a] = __double2float_ru(sh[a]);
+                }
+                if (gap2_lower(aolo, aohi, rlo, rhi, sd, su) >= bx.thi) continue;
+                if (maxgap2_upper(ailo, aihi, rlo, rhi, sd, su) < bx.tlo) {
+                    myq[nq++] = make_int4(0, (int)nl - 1, code, lane);
+                    continue;
+                }
+                in_tree = true;
+                sp = 0;
+                cur = make_int2(nl >= 2 ? 0 : kLeafBit, -1);
+                visits = 0;
+            }
+            if (++visits > 2 * nl) {
+                atomicOr(err, 4u);
+                bad = done = true;
+                break;
+            }
+            int2 next = make_int2(0, -2);  // y == -2: take the next stacked entry
+            if (cur.y >= 0) {  // a whole leaf range deferred behind a left subtree
+                myq[nq++] = make_int4(cur.x, cur.y, code, lane);
+            } else if (cur.x < 0) {  // a leaf that passed the lower-bound test
+                const int J = cur.x & 0x7fffffff;
+                const float4 r0 = lrec[2 * (int64_t)J], r1 = lrec[2 * (int64_t)J + 1];
+                const float bi_lo[3] = {r0.x, r0.y, r0.z}, bi_hi[3] = {r1.x, r1.y, r1.z};
+                if (gap2_upper(ailo, aihi, bi_lo, bi_hi, sd, su) < bx.tlo ||
+                    gap2_d(A, lbox + 6 * (int64_t)J, sh) < bx.rc2m)
+                    myq[nq++] = make_int4(J, J, code, lane);
+            } else {
+                const float4* qn = nodef + 4 * (int64_t)cur.x;
+                const float4 q0 = qn[0], q1 = qn[1], q2 = qn[2], q3 = qn[3];
+                const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
+                const float blo[3] = {q1.z, q1.w, q2.x}, bhi[3] = {q2.y, q2.z, q2.w};
+                const int lc = __float_as_int(q3.x), rc = __float_as_int(q3.y);
+                const int lo = __float_as_int(q3.z), hi = __float_as_int(q3.w);
+                const int gamma = lc & 0x7fffffff;
+                const bool pl = gap2_lower(aolo, aohi, llo, lhi, sd, su) < bx.thi;
+                const bool pr = gap2_lower(aolo, aohi, blo, bhi, sd, su) < bx.thi;
+                const bool fl = pl && maxgap2_upper(ailo, aihi, llo, lhi, sd, su) < bx.tlo;
+                const bool fr = pr && maxgap2_upper(ailo, aihi, blo, bhi, sd, su) < bx.tlo;
+                if (fl) myq[nq++] = make_int4(lo, gamma, code, lane);
+                if (pl && !fl) {  // the left child needs a visit; the right one waits
+                    if (pr) {
+                        if (sp >= kStackDepth) {
+                            atomicOr(err, 2u);
+                            bad = done = true;
+                            break;
+                        }
+                        stack[sp++] = fr ? make_int2(gamma + 1, hi) : make_int2(rc, -1);
+                    }
+                    next = make_int2(lc, -1);
+                } else if (fr) {
+                    myq[nq++] = make_int4(gamma + 1, hi, code, lane);
+                } else if (pr) {
+                    next = make_int2(rc, -1);
+                }
+            }
+            if (next.y != -2) {
+                cur = next;
+            } else if (sp > 0) {
+                cur = stack[--sp];
+            } else {
+                in_tree = false;
+            }
+        }
+        // ---- the warp classifies the queued ranges of all its lanes
+        __syncwarp();
+        long long mine = 0;  // leaves this lane queued
+        for (int k = 0; k < nq; ++k) mine += (long long)myq[k].y - myq[k].x + 1;
+        long long base = mine;  // inclusive scan over lanes, then exclusive
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(kFull, base, o);
+            if (lane >= o) base += v;
+        }
+        const long long total = __shfl_sync(kFull, base, 31);
+        base -= mine;
+        {
+            long long run = base;
+            for (int k = 0; k < kQ; ++k) {
+                spre[wp][lane * kQ + k] = run;  // empty slots: zero-length, next lane's base
+                if (k < nq) run += (long long)myq[k].y - myq[k].x + 1;
+            }
+        }
+        __syncwarp();
+        for (long long v0 = 0; v0 < total; v0 += 32) {
+            const long long v = v0 + lane;
+            const bool valid = v < total;
+            int slot = 0;
+            if (valid) {  // the last slot whose prefix is <= v
+                int lo = 0, hi = kSlots - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (spre[wp][mid] <= v) lo = mid;
+                    else hi = mid - 1;
+                }
+                slot = lo;
+            }
+            const int4 r = sq[wp][slot];
+            const int owner = valid ? r.w : 32;
+            const int J = r.x + (int)(v - spre[wp][slot]);
+            bool far = false;
+            int nsrc = 0;
+            if (valid) {
+                const int s3[3] = {r.z / 9 - 1, (r.z / 3) % 3 - 1, r.z % 3 - 1};
+                float fd[3], fu[3];
+                for (int a = 0; a < 3; ++a) {
+                    fd[a] = s3[a] < 0 ? -Lru : (s3[a] > 0 ? Lrd : 0.f);
+                    fu[a] = s3[a] < 0 ? -Lrd : (s3[a] > 0 ? Lru : 0.f);
+                }
+                const float4 b0 = sbox[wp][owner][0], b1 = sbox[wp][owner][1];
+                const float alo[3] = {b0.x, b0.y, b0.z}, ahi[3] = {b1.x, b1.y, b1.z};
+                far = far_pair(alo, ahi, b1.w, lout[2 * (int64_t)J], lout[2 * (int64_t)J + 1],
+                               fd, fu, bx.theta2, bx.rc2far);
+                if (!WRITE && !far) nsrc = lfirst[J + 1] - lfirst[J];
+            }
+            const unsigned seg = __match_any_sync(kFull, owner);
+            const unsigned fb = __ballot_sync(kFull, valid && far) & seg;
+            const unsigned nb = __ballot_sync(kFull, valid && !far) & seg;
+            const unsigned lt = (1u << lane) - 1u;
+            const bool lead = valid && lane == __ffs(seg) - 1;
+            if (WRITE && valid) {
+                const uint32_t ent = ((uint32_t)J << 5) | (uint32_t)r.z;
+                if (far) {
+                    const long long pos = sfw[wp][owner] + __popc(fb & lt);
+                    if (pos < sfwe[wp][owner]) fpairs[pos] = ent;
+                    else atomicOr(err, 4u);
+                } else {
+                    const long long pos = sw[wp][owner] + __popc(nb & lt);
+                    if (pos < swe[wp][owner]) pairs[pos] = ent;
+                    else atomicOr(err, 4u);
+                }
+            }
+            if (!WRITE && nsrc) atomicAdd((unsigned long long*)&ssrc[wp][owner], (unsigned long long)nsrc);
+            __syncwarp();
+            if (lead) {
+                sw[wp][owner] += __popc(nb);
+                sfw[wp][owner] += __popc(fb);
+                sc[wp][owner] += __popc(nb);
+                scf[wp][owner] += __popc(fb);
+            }
+            __syncwarp();
+        }
+        if (__all_sync(kFull, done)) break;
+    }
+    if (!live) return;
+    const int64_t c = sc[wp][lane], cf = scf[wp][lane], src = ssrc[wp][lane];
+    if (WRITE && !bad && (sw[wp][lane] != swe[wp][lane] || sfw[wp][lane] != sfwe[wp][lane]))
+        atomicOr(err, 4u);
+    if (!WRITE) {
+        const int64_t nI = lfirst[I + 1] - lfirst[I];
+        lcnt[I] = c;
+        lfar[I] = cf;
+        lcost[I] = src * nI;
+        atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
+        atomicAdd((unsigned long long*)(cnt + kCntFar), (unsigned long long)cf);
         atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
         atomicMax(cnt + kCntMaxCost, (long long)(src * nI));
         atomicMax(cnt + kCntMaxRow, (long long)c);
@@ -1113,11 +1319,15 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
         k_tree_pack<<<nblk(nl - 1, 256), 256, 0, st>>>(nl, tnode, tspan, lbox, tbox, nodef);
     }
     const double* rootbox = nl >= 2 ? tbox : lbox;
-    k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec,
-                                                  (const float4*)(s + S.lout), nodef, rootbox,
-                                                  lcnt, lcost, nullptr, nullptr,
-                                                  (int64_t*)(s + S.lfar), nullptr, nullptr, cnt,
-                                                  (unsigned*)(cnt + kCntError));
+    if (theta > 0.0)
+        k_pairs_split<false><<<nblk(nl, 128), 128, 0, st>>>(
+            nl, bx, lfirst, lbox, lrec, (const float4*)(s + S.lout), nodef, rootbox, lcnt, lcost,
+            (int64_t*)(s + S.lfar), nullptr, nullptr, nullptr, nullptr, cnt,
+            (unsigned*)(cnt + kCntError));
+    else
+        k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec, nodef,
+                                                      rootbox, lcnt, lcost, nullptr, nullptr, cnt,
+                                                      (unsigned*)(cnt + kCntError));
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair count kernel");
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 2) return dfail(PSR_E_DEVICE, "tree traversal stack overflow");
@@ -1225,14 +1435,21 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
                                               (double4*)(w + L.fcen), (float4*)(w + L.fofs));
         if ((e = (int)cudaGetLastError())) return dcuda(e, "expansion centre kernel");
     }
-    BoxK bxw = bx;
-    bxw.theta2 = (float)(h->theta * h->theta);
-    k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
-        nl, n, bxw, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.lout),
-        (const float4*)(s + S.nodef),
-        nl >= 2 ? (const double*)(s + S.tbox) : lbox, nullptr, nullptr, rowptr,
-        (uint32_t*)(w + L.pairs), nullptr, frow, h->has_far ? (uint32_t*)(w + L.fpairs) : nullptr,
-        nullptr, (unsigned*)(w + L.ctrl) + kCtrlError);
+    const double* rootbox = nl >= 2 ? (const double*)(s + S.tbox) : lbox;
+    if (h->has_far) {
+        BoxK bxw = bx;
+        bxw.theta2 = (float)(h->theta * h->theta);
+        k_pairs_split<true><<<nblk(nl, 128), 128, 0, st>>>(
+            nl, bxw, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.lout),
+            (const float4*)(s + S.nodef), rootbox, nullptr, nullptr, nullptr, rowptr,
+            (uint32_t*)(w + L.pairs), frow, (uint32_t*)(w + L.fpairs), nullptr,
+            (unsigned*)(w + L.ctrl) + kCtrlError);
+    } else {
+        k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
+            nl, n, bx, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.nodef),
+            rootbox, nullptr, nullptr, rowptr, (uint32_t*)(w + L.pairs), nullptr,
+            (unsigned*)(w + L.ctrl) + kCtrlError);
+    }
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair write kernel");
     // schedule: the particle sort buffers are free again (values in int32
     // views of the flag / lid regions, both >= 4 nl bytes)
