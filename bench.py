@@ -53,6 +53,9 @@ def parse():
                    help="timed steps of the split short range (P2P near + multipole far)")
     p.add_argument("--split-theta", type=float, default=0.5)
     p.add_argument("--split-orders", default="4,6")
+    p.add_argument("--paper-steps", type=int, default=3,
+                   help="timed steps of each prior-art variant (the paper's block-per-leaf "
+                        "kernel, ORB leaves)")
     p.add_argument("--pm-steps", type=int, default=5,
                    help="steps of the long-range PM part on the same box (0: skip)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
@@ -375,6 +378,59 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
                               "status": int(status.item())})
     del lv
     return out, totals
+
+
+def run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush, full_ms):
+    """The paper's own design on the same workload (prior art): its
+    block-per-target-leaf kernel (Algorithms 1 and 2) with the headline table
+    and with its Taylor T[2] table, on the octree leaves and on the paper's
+    ORB leaves (host-built, the same leaf limit), beside the warp-per-leaf
+    kernel on ORB leaves.  Every variant computes the same forces; ms per
+    step is the comparison (evaluated pairs differ between trees)."""
+    t0 = time.perf_counter()
+    orb = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf, fp64=False,
+                           orb=True)
+    orb_build_s = time.perf_counter() - t0
+    orb.upload(dev)
+    taylor = dict(precision=psr.PSR_FP32_TABLE, table_n=384, interp=psr.PSR_TAYLOR2)
+    head = dict(precision=opts.precision, table_n=opts.table_n, interp=opts.interp,
+                accum=opts.accum)
+    runs = [("octree", lv, "paper block-per-leaf", dict(head, kernel=psr.PSR_KERNEL_PAPER)),
+            ("octree", lv, "paper block-per-leaf, Taylor T[2] 384",
+             dict(taylor, kernel=psr.PSR_KERNEL_PAPER)),
+            ("orb", orb, "warp-per-leaf (headline kernel)", head),
+            ("orb", orb, "paper block-per-leaf", dict(head, kernel=psr.PSR_KERNEL_PAPER)),
+            ("orb", orb, "paper block-per-leaf, Taylor T[2] 384",
+             dict(taylor, kernel=psr.PSR_KERNEL_PAPER))]
+    out, accs = [], []
+    for tree, L_, name, kw in runs:
+        o = psr.Options(**kw)
+        acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            L_.forces(o, out=acc)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for k in range(args.paper_steps):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L_.forces(o, out=acc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms /= args.paper_steps
+        L_.check()
+        ev = int(L_.info.evaluated_pairs)
+        out.append({"tree": tree, "kernel": name, "ms_per_step": ms,
+                    "value": ev / (ms / 1e3) / 1e9, "unit": "G pair-interactions/s",
+                    "evaluated_pairs": ev, "slowdown_vs_headline": ms / full_ms})
+        accs.append(acc.double().cpu().numpy())
+    oi = orb.info
+    line = {"orb_leaves": int(oi.n_leaves), "orb_leaf_pairs": int(oi.n_pairs),
+            "orb_evaluated_pairs": int(oi.evaluated_pairs), "orb_host_build_s": orb_build_s,
+            "headline_ms": full_ms, "variants": out}
+    del orb
+    return line, accs
 
 
 def capi_ncoef(p):
@@ -713,6 +769,11 @@ def run_psr(args):
         fmm_line = run_fmm(args, torch, dev, b, lv, stream, flush,
                            rank == 0 and not args.no_cpu_baseline)
 
+    paper_line = paper_acc = None
+    if args.paper_steps > 0 and b.n <= (1 << 22):
+        paper_line, paper_acc = run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush,
+                                                 mean_ms)
+
     split_line = split_acc = None
     if args.split_steps > 0 and b.n <= (1 << 22):
         split_line, split_acc = run_split(args, torch, psr, dev, b, opts, stream, flush, mean_ms,
@@ -721,6 +782,10 @@ def run_psr(args):
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
         cb, err, tg, ref = cpu_baseline(b, acc32, args.cpu_targets, return_ref=True)
+        if paper_line:
+            for v, a_ in zip(paper_line["variants"], paper_acc):
+                d = a_[tg] - ref
+                v["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
         if split_line:
             for o in split_line["orders"]:
                 d = split_acc[o["order"]][tg] - ref
@@ -763,6 +828,7 @@ def run_psr(args):
         "pm_long_range": pm_line,
         "fmm_operators": fmm_line,
         "split_short_range": split_line,
+        "paper_design": paper_line,
         "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
                         "sampled_targets": None if cb is None else args.cpu_targets},

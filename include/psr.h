@@ -70,6 +70,12 @@ extern "C" {
 /* inner loop of the FP32 forward kernels */
 #define PSR_KERNEL_AUTO 0   /* the library's default (scalar streams)          */
 #define PSR_KERNEL_SCALAR 1 /* one source particle per lane and iteration      */
+#define PSR_KERNEL_PAPER 3  /* the paper's mapping (Section 3.2, Algorithms 1
+                               and 2): one thread block per target leaf, one
+                               thread per target particle, each source leaf
+                               staged in shared memory between two barriers;
+                               same pair arithmetic and tables (prior art,
+                               kept for comparison)                           */
 #define PSR_KERNEL_PACKED 2 /* two source particles per lane and iteration in
                                packed f32x2 arithmetic (sm_100+)               */
 /* accumulation of FP32 partial sums across source leaves */
@@ -98,7 +104,7 @@ typedef struct {
     int fold_every;      /* source particles summed in FP32 before a fold;
                             0 = default (64)                                  */
     int count_pairs;     /* 1: also count pairs with 0 < r < r_c (slower)     */
-    int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED (FP32 forward) */
+    int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED | _PAPER (FP32 forward) */
     int source_tile;     /* FP32 kernels: source particles staged per warp in
                             shared memory, 64 | 128 | 256 and >= the largest
                             leaf; 0 = default (forward 256, adjoint 128)    */
@@ -136,6 +142,11 @@ typedef struct {
 typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
 
 /* Build flags */
+#define PSR_BUILD_ORB 2     /* host builder: the paper's ORB tree (Section 2:
+                               a cell's particles split in two equal halves
+                               along the longest axis of their box) instead
+                               of the Morton octree; leaf centres (lcen) are
+                               the leaf boxes' centres on the L / 2^22 grid */
 #define PSR_BUILD_NO_FP64 1 /* omit the FP64 particle copy (PSR_FP64 and the
                                FP64 adjoint are then unavailable)            */
 

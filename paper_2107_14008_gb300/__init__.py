@@ -13,13 +13,13 @@ import numpy as np
 
 from . import capi
 from .capi import (PSR_ACC_FP64, PSR_ACC_KAHAN32, PSR_CUBIC, PSR_FP32_EXACT, PSR_FP32_TABLE,
-                   PSR_FP64, PSR_KERNEL_AUTO, PSR_KERNEL_PACKED, PSR_KERNEL_SCALAR, PSR_LINEAR,
-                   PSR_TAYLOR2, PSR_TAYLOR4, PsrError)
+                   PSR_FP64, PSR_KERNEL_AUTO, PSR_KERNEL_PACKED, PSR_KERNEL_PAPER,
+                   PSR_KERNEL_SCALAR, PSR_LINEAR, PSR_TAYLOR2, PSR_TAYLOR4, PsrError)
 
 __all__ = ["Options", "Leaves", "PM", "P2PForce", "forces", "PsrError", "PSR_FP64", "PSR_FP32_EXACT",
            "PSR_FP32_TABLE", "PSR_LINEAR", "PSR_CUBIC", "PSR_TAYLOR2", "PSR_TAYLOR4",
            "PSR_ACC_FP64", "PSR_ACC_KAHAN32",
-           "PSR_KERNEL_AUTO", "PSR_KERNEL_SCALAR", "PSR_KERNEL_PACKED"]
+           "PSR_KERNEL_AUTO", "PSR_KERNEL_SCALAR", "PSR_KERNEL_PACKED", "PSR_KERNEL_PAPER"]
 
 
 @dataclass
@@ -91,7 +91,9 @@ class Leaves:
         self._info = capi.psr_leaves_info(handle)
 
     @classmethod
-    def build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True):
+    def build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, orb=False):
+        """Host build (psr_build_leaves): the Morton octree, or with orb=True
+        the paper's ORB tree (PSR_BUILD_ORB)."""
         p = _host_f64(pos, 3)
         m = None if mass is None else _host_f64(mass, 1)
         if m is not None and m.shape[0] != p.shape[0]:
@@ -100,7 +102,8 @@ class Leaves:
         h = capi.psr_build_leaves(p.ctypes.data_as(dp),
                                   None if m is None else m.ctypes.data_as(dp), p.shape[0],
                                   _box(L, r_s, r_c, G), int(max_leaf),
-                                  0 if fp64 else capi.PSR_BUILD_NO_FP64)
+                                  (0 if fp64 else capi.PSR_BUILD_NO_FP64) |
+                                  (capi.PSR_BUILD_ORB if orb else 0))
         return cls(h, p.shape[0])
 
     @classmethod

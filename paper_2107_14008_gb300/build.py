@@ -25,7 +25,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--ftz=tr
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function",
              "-ffp-contract=off",
              "-I" + os.path.join(ROOT, "include")]
-CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_f64.cu",
+CU_SOURCES = ["p2p_fwd_f32.cu", "p2p_fwd_f32_sc.cu", "p2p_fwd_f32_pk.cu", "p2p_fwd_blk.cu", "p2p_fwd_f64.cu",
               "p2p_adj.cu", "capi.cu", "noalloc.cu", "devbuild.cu", "pm.cu", "fmm.cu"]
 CXX_SOURCES = ["builder.cpp"]
 

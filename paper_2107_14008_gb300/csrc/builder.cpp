@@ -8,8 +8,10 @@
 // (TaskGroup) with an index of start and length per i-leaf (GroupIdx).
 //
 // This builder uses an octree cut along a 63-bit Morton order (21 bits per
-// axis) instead of the paper's ORB tree; the sum it feeds is tree-independent
-// up to rounding order.  The near-field list holds, for every target leaf,
+// axis) by default; with PSR_BUILD_ORB it builds the paper's ORB tree (each
+// cell's particles split into two halves of equal count along the longest
+// axis of their box).  The sum it feeds is tree-independent up to rounding
+// order.  The near-field list holds, for every target leaf,
 // every (source leaf, periodic image) whose tight bounding boxes come closer
 // than r_c, so no pair within the cutoff is missed.
 #include <algorithm>
@@ -137,7 +139,8 @@ struct LeafRec {
     int64_t first;  // global sorted index
     int32_t count;
     int32_t level;
-    uint32_t ix, iy, iz;
+    uint32_t ix, iy, iz;  // octree cell (octree leaves)
+    int32_t cen[3];       // reference point in units of L / 2^22 (ORB leaves), or -1
     double lo[3], hi[3];
 };
 
@@ -176,6 +179,7 @@ struct Tree {
         lf.ix = ix;
         lf.iy = iy;
         lf.iz = iz;
+        lf.cen[0] = lf.cen[1] = lf.cen[2] = -1;
         leaf_box(lf);
         Node nd;
         for (int a = 0; a < 3; ++a) {
@@ -211,6 +215,97 @@ struct Tree {
                                          2 * iy + ((c >> 1) & 1), 2 * iz + (c & 1)));
                 s = t;
             }
+        }
+        Node nd;
+        for (int a = 0; a < 3; ++a) {
+            nd.lo[a] = INFINITY;
+            nd.hi[a] = -INFINITY;
+        }
+        for (int32_t k : kids)
+            for (int a = 0; a < 3; ++a) {
+                nd.lo[a] = std::min(nd.lo[a], nodes[k].lo[a]);
+                nd.hi[a] = std::max(nd.hi[a], nodes[k].hi[a]);
+            }
+        nd.first_child = (int32_t)children.size();
+        nd.nchild = (int32_t)kids.size();
+        nd.leaf = -1;
+        children.insert(children.end(), kids.begin(), kids.end());
+        nodes.push_back(nd);
+        return (int32_t)nodes.size() - 1;
+    }
+
+    // ---- ORB (paper, Section 2) over the local particles in `ord` order:
+    // a cell's particles go in equal halves (the second one larger by one
+    // for an odd count) to two children, split at the median of the longest
+    // axis of their box (ties by index), until at most max_leaf remain.
+    // ord[k] is the local index of the particle at ORB position k.
+    std::vector<int32_t> ord;
+    double unit = 1.0;  // L / 2^22
+
+    int32_t make_orb_leaf(int64_t b, int64_t e, int level)
+    {
+        LeafRec lf;
+        lf.first = base + b;
+        lf.count = (int32_t)(e - b);
+        lf.level = level;
+        lf.ix = lf.iy = lf.iz = 0;
+        for (int a = 0; a < 3; ++a) {
+            lf.lo[a] = INFINITY;
+            lf.hi[a] = -INFINITY;
+        }
+        for (int64_t k = b; k < e; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const double v = xs[3 * (int64_t)ord[k] + a];
+                lf.lo[a] = std::min(lf.lo[a], v);
+                lf.hi[a] = std::max(lf.hi[a], v);
+            }
+        // reference point: the box centre rounded to the integer grid
+        for (int a = 0; a < 3; ++a) {
+            double c = std::floor(0.5 * (lf.lo[a] + lf.hi[a]) / unit + 0.5);
+            c = std::min(std::max(c, 0.0), (double)((1 << kCentreShift) - 1));
+            lf.cen[a] = (int32_t)c;
+        }
+        Node nd;
+        for (int a = 0; a < 3; ++a) {
+            nd.lo[a] = lf.lo[a];
+            nd.hi[a] = lf.hi[a];
+        }
+        nd.first_child = -1;
+        nd.nchild = 0;
+        nd.leaf = leaf_base + (int32_t)leaves.size();
+        leaves.push_back(lf);
+        nodes.push_back(nd);
+        return (int32_t)nodes.size() - 1;
+    }
+
+    int32_t build_orb(int64_t b, int64_t e, int level)
+    {
+        if (e - b <= max_leaf) return make_orb_leaf(b, e, level);
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t k = b; k < e; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const double v = xs[3 * (int64_t)ord[k] + a];
+                lo[a] = std::min(lo[a], v);
+                hi[a] = std::max(hi[a], v);
+            }
+        int ax = 0;
+        for (int a = 1; a < 3; ++a)
+            if (hi[a] - lo[a] > hi[ax] - lo[ax]) ax = a;
+        std::vector<int32_t> kids;
+        if (!(hi[ax] > lo[ax])) {
+            // coincident positions: chunks of max_leaf particles
+            for (int64_t s = b; s < e; s += max_leaf)
+                kids.push_back(make_orb_leaf(s, std::min(e, s + max_leaf), level + 1));
+        } else {
+            const int64_t mid = b + (e - b) / 2;
+            const double* x = xs;
+            std::nth_element(ord.begin() + b, ord.begin() + mid, ord.begin() + e,
+                             [x, ax](int32_t i, int32_t j) {
+                                 const double u = x[3 * (int64_t)i + ax], v = x[3 * (int64_t)j + ax];
+                                 return u < v || (u == v && i < j);
+                             });
+            kids.push_back(build_orb(b, mid, level + 1));
+            kids.push_back(build_orb(mid, e, level + 1));
         }
         Node nd;
         for (int a = 0; a < 3; ++a) {
@@ -301,6 +396,10 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
     *out = nullptr;
     if (max_leaf < 1 || max_leaf > kMaxLeaf) {
         *err = "max_leaf must be in [1, 64]";
+        return PSR_E_ARG;
+    }
+    if (flags & ~(PSR_BUILD_NO_FP64 | PSR_BUILD_ORB)) {
+        *err = "unknown build flags";
         return PSR_E_ARG;
     }
     int64_t ntot = 0;
@@ -425,13 +524,38 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
             t.max_leaf = max_leaf;
             t.leaf_base = leaf_total;
             if (n[b] == 0) continue;  // an empty box has no leaves
-            t.root = t.build(0, n[b], 0, 0, 0, 0);
+            if (flags & PSR_BUILD_ORB) {
+                t.unit = std::ldexp(boxes[b].L, -kCentreShift);
+                t.ord.resize(n[b]);
+                for (int64_t k = 0; k < n[b]; ++k) t.ord[k] = (int32_t)k;  // from Morton order
+                t.root = t.build_orb(0, n[b], 0);
+            } else {
+                t.root = t.build(0, n[b], 0, 0, 0, 0);
+            }
             leaf_total += (int32_t)t.leaves.size();
             if (leaf_total >= (1 << 27)) {
                 delete h;
                 *err = "more than 2^27 leaves";
                 return PSR_E_ARG;
             }
+        }
+        if (flags & PSR_BUILD_ORB) {
+            // particles into ORB order, box by box
+            std::vector<double> sx2(sx.size());
+            std::vector<int64_t> perm2(h->perm.size());
+            for (int b = 0; b < nbox; ++b) {
+                const Tree& t = trees[b];
+                const int64_t base = h->box_first[b];
+                for (int64_t k = 0; k < n[b]; ++k) {
+                    const int64_t o = base + t.ord[k];
+                    for (int a = 0; a < 3; ++a) sx2[3 * (base + k) + a] = sx[3 * o + a];
+                    perm2[base + k] = h->perm[o];
+                }
+            }
+            sx.swap(sx2);
+            h->perm.swap(perm2);
+            for (Tree& t : trees) t.xs = nullptr;  // the trees' boxes are final
+            for (int64_t k = 0; k < ntot; ++k) h->perm32[k] = (int32_t)h->perm[k];
         }
         const int64_t nl = leaf_total;
         h->leaf.resize(nl * 4);
@@ -451,10 +575,14 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
             h->leaf[4 * g + 1] = lf.count;
             h->leaf[4 * g + 2] = lbox[g];
             h->leaf[4 * g + 3] = 0;
-            uint32_t sc = 1u << (kMortonBits - lf.level);  // 2^(21-l)
-            h->lcen[4 * g + 0] = (int32_t)((2 * lf.ix + 1) * sc);
-            h->lcen[4 * g + 1] = (int32_t)((2 * lf.iy + 1) * sc);
-            h->lcen[4 * g + 2] = (int32_t)((2 * lf.iz + 1) * sc);
+            if (lf.cen[0] >= 0) {  // ORB leaf: its box centre on the integer grid
+                for (int a = 0; a < 3; ++a) h->lcen[4 * g + a] = lf.cen[a];
+            } else {
+                uint32_t sc = 1u << (kMortonBits - lf.level);  // 2^(21-l)
+                h->lcen[4 * g + 0] = (int32_t)((2 * lf.ix + 1) * sc);
+                h->lcen[4 * g + 1] = (int32_t)((2 * lf.iy + 1) * sc);
+                h->lcen[4 * g + 2] = (int32_t)((2 * lf.iz + 1) * sc);
+            }
             h->lcen[4 * g + 3] = lf.level;
             maxl = std::max(maxl, lf.count);
         }

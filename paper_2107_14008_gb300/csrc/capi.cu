@@ -59,7 +59,7 @@ int check_opts(const psr_opts* o, Opts* out)
     if (o->source_tile != 0 && o->source_tile != 64 && o->source_tile != 128 &&
         o->source_tile != 256)
         return fail(PSR_E_ARG, "psr_opts.source_tile must be 0, 64, 128 or 256");
-    if (o->kernel < PSR_KERNEL_AUTO || o->kernel > PSR_KERNEL_PACKED)
+    if (o->kernel < PSR_KERNEL_AUTO || o->kernel > PSR_KERNEL_PAPER)
         return fail(PSR_E_ARG, "psr_opts.kernel out of range");
     if (o->precision < PSR_FP64 || o->precision > PSR_FP32_TABLE)
         return fail(PSR_E_ARG, "psr_opts.precision out of range");
@@ -174,6 +174,8 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
                               o.tile ? o.tile : kAdjStageCap, &occ);
         else if (o.precision == PSR_FP64)
             e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
+        else if (o.kernel == PSR_KERNEL_PAPER)
+            e = fwd_blk_occupancy(o.precision, o.interp, o.accum, h->max_leaf, o.table_n, &occ);
         else {
             int cap;
             if ((e = fwd32_smem_config(o, &cap))) return e;
@@ -339,7 +341,9 @@ int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stre
         cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 8, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (pair counter)");
     }
-    int e = (o.precision == PSR_FP64) ? launch_fwd_f64(a, st) : launch_fwd_f32(a, o.precision, st);
+    int e = (o.precision == PSR_FP64)          ? launch_fwd_f64(a, st)
+            : (o.kernel == PSR_KERNEL_PAPER) ? launch_fwd_blk(a, o.precision, st)
+                                             : launch_fwd_f32(a, o.precision, st);
     if (e) return cuda_fail((cudaError_t)e, "forward kernel launch");
     return PSR_OK;
 }

@@ -1252,6 +1252,8 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     if (!d_pos || !box || n < 1 || n > kMaxN)
         return dfail(PSR_E_ARG, "null argument or n outside [1, 2^28]");
     if (max_leaf < 1 || max_leaf > kMaxLeaf) return dfail(PSR_E_ARG, "max_leaf must be in [1, 64]");
+    if (flags & ~PSR_BUILD_NO_FP64)
+        return dfail(PSR_E_ARG, "the device builder takes PSR_BUILD_NO_FP64 only (no ORB)");
     if (!(std::isfinite(box->L) && box->L > 0) || !(std::isfinite(box->r_s) && box->r_s > 0) ||
         !std::isfinite(box->G))
         return dfail(PSR_E_ARG, "L, r_s must be finite and positive");

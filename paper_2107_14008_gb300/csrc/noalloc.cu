@@ -114,7 +114,9 @@ extern "C" int psr_p2p_forces_noalloc(psr_leaves* hh, const psr_opts* opts, void
             return PSR_E_CUDA;
         }
     }
-    int le = precision == PSR_FP64 ? launch_fwd_f64(a, st) : launch_fwd_f32(a, precision, st);
+    int le = precision == PSR_FP64              ? launch_fwd_f64(a, st)
+             : a.variant == PSR_KERNEL_PAPER ? launch_fwd_blk(a, precision, st)
+                                             : launch_fwd_f32(a, precision, st);
     if (le) {
         set_last_error(std::string("forward kernel launch: ") + cudaGetErrorString((cudaError_t)le));
         return PSR_E_CUDA;

@@ -160,7 +160,7 @@ struct FwdArgs {
     int warps_per_block;
     int blocks;
     int max_leaf;
-    int variant;     // FP32 forward: PSR_KERNEL_SCALAR or PSR_KERNEL_PACKED
+    int variant;     // FP32 forward: PSR_KERNEL_SCALAR, _PACKED or _PAPER
     int stage_cap;   // FP32 kernels: staged particles per warp
     int item_stride; // this launch takes schedule entries ticket * stride + offset
     int item_offset;
@@ -176,6 +176,8 @@ int fwd_f32_occupancy(int precision, int interp, int accum, int warps, int max_l
 size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap);
 constexpr size_t kSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block
 int fwd_f64_occupancy(int warps, int max_leaf, int* out);
+int launch_fwd_blk(const FwdArgs& a, int precision, void* stream);  // p2p_fwd_blk.cu
+int fwd_blk_occupancy(int precision, int interp, int accum, int max_leaf, int table_n, int* out);
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
                   int cap, int* out);
 size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap);

@@ -362,3 +362,80 @@ def test_table_argument_checks():
     with pytest.raises(capi.PsrError) as e:
         capi.psr_table(384, capi.PSR_TAYLOR2, -1.0, fake, 0)
     assert e.value.code == capi.PSR_E_ARG
+
+
+def _orb_leaf_sizes(n, max_leaf):
+    """Leaf sizes of equal-halves bisection (paper, Section 2: a cell's
+    particles are split equally between two children until at most
+    MAXLEAF remain), in leaf order, by recursion on the counts alone."""
+    if n <= max_leaf:
+        return [n]
+    return _orb_leaf_sizes(n // 2, max_leaf) + _orb_leaf_sizes(n - n // 2, max_leaf)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("max_leaf", [1, 8, 32, 64])
+def test_orb_leaves_are_equal_halves(case, max_leaf):
+    """PSR_BUILD_ORB: the leaf sizes are those of equal halving (so that no
+    two leaves differ by more than one particle for a count that is not a
+    power-of-two multiple); each leaf's particles lie in its box; every
+    particle once; the FP32 local coordinates round the offset from the
+    leaf's reference point (its box centre on the L / 2^22 grid) once."""
+    b = CASES[case]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf, orb=True)
+    A = lv.host_arrays()
+    perm = lv.perm
+    assert np.array_equal(np.sort(perm), np.arange(b.n))
+    leaf = A["leaf"]
+    assert list(leaf[:, 1]) == _orb_leaf_sizes(b.n, max_leaf)
+    assert np.all(leaf[1:, 0] == leaf[:-1, 0] + leaf[:-1, 1])
+    wrapped = np.mod(b.pos, b.L)[perm]
+    np.testing.assert_array_equal(A["pd"][:, :3], wrapped)
+    unit = b.L / 2.0 ** 22
+    owner = np.repeat(np.arange(leaf.shape[0]), leaf[:, 1])
+    lo = np.minimum.reduceat(wrapped, leaf[:, 0], axis=0)
+    hi = np.maximum.reduceat(wrapped, leaf[:, 0], axis=0)
+    ref = np.clip(np.floor(0.5 * (lo + hi) / unit + 0.5), 0, 2 ** 22 - 1)
+    np.testing.assert_array_equal(A["lcen"][:, :3], ref.astype(np.int32))
+    loc = A["pf"][:, :3].astype(np.float64) * 2 * b.r_s
+    cen = A["lcen"][owner, :3] * unit
+    span = np.max(hi - lo, axis=1)[owner] + unit
+    assert np.all(np.abs(loc + cen - wrapped) <= 1.2e-7 * span[:, None] + 1e-12 * b.L)
+
+
+def test_orb_splits_along_the_longest_axis():
+    """A slab 8 x 1 x 1: the first three splits cut x (extents 8, 4, 2
+    against 1), so the first eighth of the particles in ORB order are those
+    of smallest x."""
+    rng = np.random.default_rng(9)
+    n = 1024
+    pos = rng.random((n, 3)) * [8.0, 1.0, 1.0] + [1.0, 1.0, 1.0]
+    L = 20.0
+    r_s, r_c = synth.box_params(L, 16)
+    lv = psr.Leaves.build(pos, None, L, r_s, r_c, 1.0, max_leaf=32, orb=True)
+    assert set(lv.perm[:n // 8]) == set(np.argsort(pos[:, 0])[:n // 8])
+    assert set(lv.perm[:n // 2]) == set(np.argsort(pos[:, 0])[:n // 2])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_orb_pair_list_is_complete(case):
+    b = CASES[case]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=16, orb=True)
+    counts = _count_listed_pairs(lv, b)
+    _, ref, zero = oracle.forces(b.pos % b.L, b.mass, b.L, b.r_s, b.r_c)
+    np.testing.assert_array_equal(counts, ref[lv.perm])
+
+
+def test_build_flag_checks():
+    b = CASES["uniform"]()
+    with pytest.raises(psr.PsrError) as e:
+        capi.psr_build_leaves(np.ascontiguousarray(b.pos).ctypes.data_as(
+            __import__("ctypes").POINTER(__import__("ctypes").c_double)), None, b.n,
+            capi.psr_box(b.L, b.r_s, b.r_c, 1.0), 32, 4)
+    assert e.value.code == capi.PSR_E_ARG
+    box = capi.psr_box(10.0, 0.5, 2.25, 1.0)
+    fake = 1 << 40  # never dereferenced: the flag check fails first
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_device_build(fake, 0, 100, box, 32, capi.PSR_BUILD_ORB, fake,
+                              capi.psr_device_build_scratch_bytes(100), 0, 1000)
+    assert e.value.code == capi.PSR_E_ARG

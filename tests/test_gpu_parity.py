@@ -93,7 +93,7 @@ FP32_VARIANTS = [
 ]
 
 
-KERNELS = [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED]
+KERNELS = [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED, psr.PSR_KERNEL_PAPER]
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -122,7 +122,7 @@ def test_wide_leaves_two_targets_per_lane(case, kernel, interp):
 @pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
                                          (psr.PSR_CUBIC, oracle.T_CUBIC)])
 @pytest.mark.parametrize("table_n", [256, 1024])
-@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_table_path_matches_interpolated_oracle(case, interp, mode, table_n, kernel):
     b = CASES[case]()
     ref, _, _ = oracle_acc(b, case, mode, table_n)
@@ -133,7 +133,8 @@ def test_table_path_matches_interpolated_oracle(case, interp, mode, table_n, ker
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("precision,kernel", [(psr.PSR_FP64, 0), (psr.PSR_FP32_TABLE, 1),
-                                              (psr.PSR_FP32_TABLE, 2), (psr.PSR_FP32_EXACT, 1)])
+                                              (psr.PSR_FP32_TABLE, 2), (psr.PSR_FP32_EXACT, 1),
+                                              (psr.PSR_FP32_TABLE, 3)])
 def test_pair_count_matches_oracle(case, precision, kernel):
     b = CASES[case]()
     _, pairs, _ = oracle_acc(b, case)
@@ -547,3 +548,48 @@ def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf):
     lv.check()
     assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4, name
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("max_leaf", [8, 32, 64])
+def test_orb_leaves_match_oracle(case, max_leaf):
+    """The paper's ORB tree (PSR_BUILD_ORB) feeds the same sum: FP64 path to
+    1e-9, the FP32 table path (warp-per-leaf and the paper's block-per-leaf
+    kernel) to the table tolerance."""
+    b = CASES[case]()
+    ref, _, _ = oracle_acc(b, case)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf,
+                          orb=True).upload()
+    a64 = lv.forces(psr.Options(precision=psr.PSR_FP64)).cpu().numpy()
+    np.testing.assert_allclose(a64, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    for kernel in KERNELS:
+        a32 = lv.forces(psr.Options(kernel=kernel)).double().cpu().numpy()
+        assert rel_rms(a32, ref) < 2e-5, kernel
+    lv.check()
+
+
+def test_paper_kernel_sharded_and_graph_replayed():
+    """Sharded launches of the block-per-leaf kernel cover every target once;
+    a CUDA graph replays it."""
+    b = CASES["clustered"]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32).upload()
+    o = psr.Options(kernel=psr.PSR_KERNEL_PAPER)
+    whole = lv.forces(o).cpu().numpy()
+    out = torch.full((b.n, 3), float("nan"), dtype=torch.float32, device="cuda")
+    for k in range(3):
+        lv.forces(psr.Options(kernel=psr.PSR_KERNEL_PAPER, shard_count=3, shard_index=k), out=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), whole)
+    out2 = torch.zeros((b.n, 3), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lv.forces(o, out=out2)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lv.forces(o, out=out2)
+    out2.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out2.cpu().numpy(), whole)
+    lv.check()
