@@ -226,10 +226,11 @@ def m2l_flops_per_entry(p):
 
 def run_fmm(args, torch, dev, b, lv, stream, flush, check):
     """Truncated multipole operators (P2M, M2L with the f_(n) prefactors, L2P)
-    on the workload's leaves: P2M on every leaf; M2L on the leaf pairs of the
-    near-field list whose cell centres are at least 1.5 x the summed cell
-    sides apart (a multipole acceptance criterion), for the first 5000
-    target leaves; L2P on those targets."""
+    on the workload's leaves: P2M on every leaf about its cell centre; M2L on
+    the leaf pairs of the near-field list that pass the split's opening test
+    with theta = 0.5 (theta min(d, 2 r_s^2 / d) >= rho_I + rho_J, rho the
+    cell's half diagonal), for the first 5000 target leaves; L2P on those
+    targets."""
     import numpy as np
     from paper_2107_14008_gb300 import capi
     p = args.fmm_order
@@ -249,7 +250,8 @@ def run_fmm(args, torch, dev, b, lv, stream, flush, check):
     code = (pairs[:e1] & 31).astype(np.int64)
     sh = np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], axis=1) * b.L
     dist = np.linalg.norm(centres[tgt] - centres[src] - sh, axis=1)
-    far = dist >= 1.5 * (side[tgt] + side[src])
+    rho = 0.5 * np.sqrt(3.0) * side
+    far = 0.5 * np.minimum(dist, 2 * b.r_s ** 2 / np.maximum(dist, 1e-300)) >= rho[tgt] + rho[src]
     frow = np.concatenate([[0], np.cumsum(np.bincount(tgt[far], minlength=nt))]).astype(np.int64)
     fpairs = pairs[:e1][far]
     h = float(np.median(side))
@@ -292,7 +294,7 @@ def run_fmm(args, torch, dev, b, lv, stream, flush, check):
            "l2p_ms": t[2], "m2l_entries_per_s": nfar / (t[1] / 1e3),
            "m2l_flops_per_entry": m2l_flops_per_entry(p),
            "m2l_tflops": m2l_flops_per_entry(p) * nfar / (t[1] / 1e3) / 1e12,
-           "mac": "centre distance >= 1.5 x (side_I + side_J)"}
+           "mac": "0.5 min(d, 2 r_s^2 / d) >= rho_I + rho_J (cell half diagonals)"}
     if check:
         from oracle import fmm as ofmm
         got = acc.double().cpu().numpy()
@@ -319,64 +321,70 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
     """The short range with the multipole split (psr_device_build_split):
     P2P (FP32 table, the headline options) over the near entries plus
     psr_fmm_forces (P2M, M2L, L2P) over the well-separated ones, against the
-    plain P2P step over the full list.  Returns the bench fields and the
-    total accelerations per order, for the oracle comparison."""
+    plain P2P step over the full list, for the opening-angle test alone and
+    with the Gaussian-length term (PSR_BUILD_SPLIT_GAUSSIAN).  Returns the
+    bench fields and the total accelerations per (rule, order), for the
+    oracle comparison."""
     pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
     mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
     theta = args.split_theta
-    lv = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
-                                 theta=theta)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(3):
-        lvb = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
-                                      theta=theta)
-        torch.cuda.synchronize()
-        del lvb
-    build_ms = (time.perf_counter() - t0) / 3 * 1e3
-    inf = lv.info
-    acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
     orders = [int(x) for x in args.split_orders.split(",") if x]
-    nl = int(inf.n_leaves)
-    scratch = torch.empty(2 * nl * ((capi_ncoef(max(orders)) + 3) // 4 * 4), dtype=torch.float32,
-                          device=dev)
-    out = {"theta": theta, "leaves": nl, "near_entries": int(inf.n_pairs),
-           "far_entries": int(inf.n_far), "evaluated_near": int(inf.evaluated_pairs),
-           "evaluated_full": int(full_evaluated),
-           "p2p_interactions_moved_to_m2l": 1.0 - inf.evaluated_pairs / full_evaluated,
-           "device_build_split_ms": build_ms, "full_p2p_ms": full_ms,
-           "acceptance": "theta |R| >= rho_I + rho_J (box half-diagonals), both boxes "
-                         "wholly within r_c", "orders": []}
+    out = {"theta": theta, "full_p2p_ms": full_ms, "evaluated_full": int(full_evaluated),
+           "rules": []}
     totals = {}
-    for p in orders:
-        def step():
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-            lv.forces(opts, out=acc)
-            e[1].record(stream)
-            lv.fmm_forces(p, out=acc, accumulate=True, scratch=scratch, status=status)
-            e[2].record(stream)
-            return e
-        for _ in range(2):
-            step()
+    for rule, gauss in (("theta |R| >= rho_I + rho_J, both boxes wholly within r_c", False),
+                        ("theta min(|R|, 2 r_s^2/|R|) >= rho_I + rho_J, both boxes wholly "
+                         "within r_c", True)):
+        mk = lambda: psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G,
+                                             max_leaf=b.max_leaf, theta=theta, gaussian_mac=gauss)
+        lv = mk()
         torch.cuda.synchronize()
-        tn = tf = 0.0
-        for k in range(args.split_steps):
-            flush.fill_(k & 255)
-            e = step()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            lvb = mk()
             torch.cuda.synchronize()
-            tn += e[0].elapsed_time(e[1])
-            tf += e[1].elapsed_time(e[2])
-        tn /= args.split_steps
-        tf /= args.split_steps
-        lv.check()
-        totals[p] = acc.double().cpu().numpy()
-        out["orders"].append({"order": p, "p2p_near_ms": tn, "fmm_far_ms": tf,
-                              "short_range_ms": tn + tf, "speedup_vs_full_p2p": full_ms / (tn + tf),
-                              "m2l_entries_per_s_upper_bound_time": inf.n_far / (tf / 1e3),
-                              "status": int(status.item())})
-    del lv
+            del lvb
+        build_ms = (time.perf_counter() - t0) / 3 * 1e3
+        inf = lv.info
+        acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        nl = int(inf.n_leaves)
+        scratch = torch.empty(2 * nl * ((capi_ncoef(max(orders)) + 3) // 4 * 4),
+                              dtype=torch.float32, device=dev)
+        r = {"acceptance": rule, "leaves": nl, "near_entries": int(inf.n_pairs),
+             "far_entries": int(inf.n_far), "evaluated_near": int(inf.evaluated_pairs),
+             "p2p_interactions_moved_to_m2l": 1.0 - inf.evaluated_pairs / full_evaluated,
+             "device_build_split_ms": build_ms, "orders": []}
+        for p in orders:
+            def step():
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                lv.forces(opts, out=acc)
+                e[1].record(stream)
+                lv.fmm_forces(p, out=acc, accumulate=True, scratch=scratch, status=status)
+                e[2].record(stream)
+                return e
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            tn = tf = 0.0
+            for k in range(args.split_steps):
+                flush.fill_(k & 255)
+                e = step()
+                torch.cuda.synchronize()
+                tn += e[0].elapsed_time(e[1])
+                tf += e[1].elapsed_time(e[2])
+            tn /= args.split_steps
+            tf /= args.split_steps
+            lv.check()
+            totals[(gauss, p)] = acc.double().cpu().numpy()
+            r["orders"].append({"order": p, "p2p_near_ms": tn, "fmm_far_ms": tf,
+                                "short_range_ms": tn + tf,
+                                "speedup_vs_full_p2p": full_ms / (tn + tf),
+                                "m2l_entries_per_s_upper_bound_time": inf.n_far / (tf / 1e3),
+                                "status": int(status.item()), "_key": [gauss, p]})
+        out["rules"].append(r)
+        del lv
     return out, totals
 
 
@@ -787,9 +795,14 @@ def run_psr(args):
                 d = a_[tg] - ref
                 v["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
         if split_line:
-            for o in split_line["orders"]:
-                d = split_acc[o["order"]][tg] - ref
-                o["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+            for r_ in split_line["rules"]:
+                for o in r_["orders"]:
+                    d = split_acc[tuple(o["_key"])][tg] - ref
+                    o["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+    if split_line:
+        for r_ in split_line["rules"]:
+            for o in r_["orders"]:
+                o.pop("_key", None)
         for v in variants:
             d = v["acc"][tg] - ref
             rel = np.linalg.norm(d, axis=1) / np.maximum(np.linalg.norm(ref, axis=1),

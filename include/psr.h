@@ -147,6 +147,16 @@ typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
                                along the longest axis of their box) instead
                                of the Morton octree; leaf centres (lcen) are
                                the leaf boxes' centres on the L / 2^22 grid */
+#define PSR_BUILD_UNPACKED 4 /* plain octree leaves.  By default both
+                               builders pack them: consecutive sibling cells
+                               that would each be a leaf share one leaf (their
+                               parent's cell) while their total stays within
+                               max_leaf, taken greedily in Morton order (a
+                               pack of one keeps its own cell); fuller leaves
+                               whose boxes stay inside the parent cell      */
+#define PSR_BUILD_SPLIT_GAUSSIAN 8 /* psr_device_build_split: also measure
+                               the cells against the Gaussian length of the
+                               kernel (see there)                           */
 #define PSR_BUILD_NO_FP64 1 /* omit the FP64 particle copy (PSR_FP64 and the
                                FP64 adjoint are then unavailable)            */
 
@@ -395,9 +405,11 @@ int psr_device_build_finish(psr_leaves* h, void* d_ws, size_t bytes, void* cuda_
  * interact through M2L, the rest through P2P).  Every leaf-pair entry the
  * walk finds within r_c goes to exactly one of two lists:
  *   far   the particle boxes' centres are R apart with theta |R| >= rho_I +
- *         rho_J (rho: half the box diagonal) and every point of one box lies
- *         within r_c of every point of the other (so the hard cutoff removes
- *         no pair of the expansion);
+ *         rho_J (rho: half the box diagonal; with PSR_BUILD_SPLIT_GAUSSIAN
+ *         also theta 2 r_s^2 / |R| >= rho_I + rho_J, 2 r_s^2 / |R| being the
+ *         length on which the kernel's Gaussian truncation varies) and every
+ *         point of one box lies within r_c of every point of the other (so
+ *         the hard cutoff removes no pair of the expansion);
  *   near  every other entry, including i = j.
  * The handle's pair list (what psr_p2p_forces and psr_p2p_adjoint evaluate)
  * holds the near entries only; the far list and the expansion centres are

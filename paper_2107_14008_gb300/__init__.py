@@ -91,9 +91,10 @@ class Leaves:
         self._info = capi.psr_leaves_info(handle)
 
     @classmethod
-    def build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, orb=False):
-        """Host build (psr_build_leaves): the Morton octree, or with orb=True
-        the paper's ORB tree (PSR_BUILD_ORB)."""
+    def build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, orb=False, pack=True):
+        """Host build (psr_build_leaves): the Morton octree with packed leaves
+        (pack=False: plain octree leaves, PSR_BUILD_UNPACKED), or with
+        orb=True the paper's ORB tree (PSR_BUILD_ORB)."""
         p = _host_f64(pos, 3)
         m = None if mass is None else _host_f64(mass, 1)
         if m is not None and m.shape[0] != p.shape[0]:
@@ -103,7 +104,8 @@ class Leaves:
                                   None if m is None else m.ctypes.data_as(dp), p.shape[0],
                                   _box(L, r_s, r_c, G), int(max_leaf),
                                   (0 if fp64 else capi.PSR_BUILD_NO_FP64) |
-                                  (capi.PSR_BUILD_ORB if orb else 0))
+                                  (capi.PSR_BUILD_ORB if orb else 0) |
+                                  (0 if pack else capi.PSR_BUILD_UNPACKED))
         return cls(h, p.shape[0])
 
     @classmethod
@@ -128,12 +130,14 @@ class Leaves:
 
     @classmethod
     def device_build(cls, pos, mass, L, r_s, r_c, G=1.0, max_leaf=32, fp64=True, stream=None,
-                     timeout_ms=60000, theta=None):
+                     timeout_ms=60000, theta=None, gaussian_mac=False, pack=True):
         """Build on the GPU from device tensors (psr_device_build and
         psr_device_build_finish): pos (n,3) and mass (n,) or None, on one CUDA
         device.  The result is already resident (no upload()).  With theta in
         (0, 1] the pair list is split (psr_device_build_split): forces() then
-        sums the near entries and fmm_forces() the well-separated ones."""
+        sums the near entries and fmm_forces() the well-separated ones;
+        gaussian_mac adds PSR_BUILD_SPLIT_GAUSSIAN, pack=False
+        PSR_BUILD_UNPACKED."""
         import torch
         if not (hasattr(pos, "is_cuda") and pos.is_cuda):
             raise ValueError("device_build takes CUDA tensors")
@@ -149,7 +153,9 @@ class Leaves:
             st = _stream_handle(stream)
             nbytes = capi.psr_device_build_scratch_bytes(n)
             scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-            flags = 0 if fp64 else capi.PSR_BUILD_NO_FP64
+            flags = (0 if fp64 else capi.PSR_BUILD_NO_FP64) | \
+                (capi.PSR_BUILD_SPLIT_GAUSSIAN if gaussian_mac else 0) | \
+                (0 if pack else capi.PSR_BUILD_UNPACKED)
             if theta is None:
                 h = capi.psr_device_build(p.data_ptr(), 0 if m is None else m.data_ptr(), n,
                                           _box(L, r_s, r_c, G), int(max_leaf), flags,

@@ -17,7 +17,7 @@ PSR_FP64, PSR_FP32_EXACT, PSR_FP32_TABLE = 0, 1, 2
 PSR_LINEAR, PSR_CUBIC, PSR_TAYLOR2, PSR_TAYLOR4 = 0, 1, 2, 3
 PSR_ACC_FP64, PSR_ACC_KAHAN32 = 0, 1
 PSR_KERNEL_AUTO, PSR_KERNEL_SCALAR, PSR_KERNEL_PACKED, PSR_KERNEL_PAPER = 0, 1, 2, 3
-PSR_BUILD_NO_FP64, PSR_BUILD_ORB = 1, 2
+PSR_BUILD_NO_FP64, PSR_BUILD_ORB, PSR_BUILD_UNPACKED, PSR_BUILD_SPLIT_GAUSSIAN = 1, 2, 4, 8
 PSR_PM_ACCUMULATE, PSR_PM_NO_DECONVOLVE = 1, 2
 PSR_FMM_ACCUMULATE, PSR_FMM_F64 = 1, 2
 

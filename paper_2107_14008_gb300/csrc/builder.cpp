@@ -8,7 +8,8 @@
 // (TaskGroup) with an index of start and length per i-leaf (GroupIdx).
 //
 // This builder uses an octree cut along a 63-bit Morton order (21 bits per
-// axis) by default; with PSR_BUILD_ORB it builds the paper's ORB tree (each
+// axis) by default, its leaves packed (consecutive sibling leaves share one
+// leaf up to MAXLEAF particles); with PSR_BUILD_ORB it builds the paper's ORB tree (each
 // cell's particles split into two halves of equal count along the longest
 // axis of their box).  The sum it feeds is tree-independent up to rounding
 // order.  The near-field list holds, for every target leaf,
@@ -150,6 +151,7 @@ struct Tree {
     const double* xs = nullptr;     // sorted wrapped positions of this box (3 per particle)
     int64_t base = 0;               // global sorted index of local particle 0
     int max_leaf = 32;
+    bool pack = false;              // pack sibling leaves (see build)
     int32_t leaf_base = 0;          // global index of this box's first leaf
     std::vector<Node> nodes;
     std::vector<int32_t> children;
@@ -207,14 +209,43 @@ struct Tree {
             int sh = 3 * (kMortonBits - 1 - level);
             uint64_t prefix = key[b] & ~((sh + 3 >= 64) ? ~0ULL : ((1ULL << (sh + 3)) - 1));
             int64_t s = b;
+            // packing: consecutive children that would be leaves share one
+            // leaf (this cell's) while their total stays within max_leaf; a
+            // pack of one child keeps the child's own cell
+            int64_t pb = -1, pe = -1;  // open pack [pb, pe)
+            int pc = 0, pk = 0;        // its single child's octant, children in it
+            auto close_pack = [&]() {
+                if (pk == 1)
+                    kids.push_back(make_leaf(pb, pe, level + 1, 2 * ix + ((pc >> 2) & 1),
+                                             2 * iy + ((pc >> 1) & 1), 2 * iz + (pc & 1)));
+                else if (pk > 1)
+                    kids.push_back(make_leaf(pb, pe, level, ix, iy, iz));
+                pk = 0;
+            };
             for (int c = 0; c < 8; ++c) {
                 uint64_t hi = prefix | ((uint64_t)(c + 1) << sh);
                 int64_t t = (c == 7) ? e : (int64_t)(std::lower_bound(key + s, key + e, hi) - key);
-                if (t > s)
-                    kids.push_back(build(s, t, level + 1, 2 * ix + ((c >> 2) & 1),
-                                         2 * iy + ((c >> 1) & 1), 2 * iz + (c & 1)));
+                if (t > s) {
+                    if (pack && t - s <= max_leaf) {
+                        if (pk > 0 && (pe - pb) + (t - s) <= max_leaf) {
+                            pe = t;
+                            ++pk;
+                        } else {
+                            close_pack();
+                            pb = s;
+                            pe = t;
+                            pc = c;
+                            pk = 1;
+                        }
+                    } else {
+                        close_pack();
+                        kids.push_back(build(s, t, level + 1, 2 * ix + ((c >> 2) & 1),
+                                             2 * iy + ((c >> 1) & 1), 2 * iz + (c & 1)));
+                    }
+                }
                 s = t;
             }
+            close_pack();
         }
         Node nd;
         for (int a = 0; a < 3; ++a) {
@@ -398,7 +429,7 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
         *err = "max_leaf must be in [1, 64]";
         return PSR_E_ARG;
     }
-    if (flags & ~(PSR_BUILD_NO_FP64 | PSR_BUILD_ORB)) {
+    if (flags & ~(PSR_BUILD_NO_FP64 | PSR_BUILD_ORB | PSR_BUILD_UNPACKED)) {
         *err = "unknown build flags";
         return PSR_E_ARG;
     }
@@ -522,6 +553,7 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
             t.xs = sx.data() + 3 * h->box_first[b];
             t.base = h->box_first[b];
             t.max_leaf = max_leaf;
+            t.pack = !(flags & PSR_BUILD_UNPACKED);
             t.leaf_base = leaf_total;
             if (n[b] == 0) continue;  // an empty box has no leaves
             if (flags & PSR_BUILD_ORB) {

@@ -117,6 +117,7 @@ struct BoxK {
     double L, scale, unit, inv2rs, rc2m;  // rc2m = r_c^2 (1 + 1e-5), the host's margin
     float thi, tlo;  // FP32 thresholds: thi >= rc2m (1 + 1e-6), tlo <= rc2m (1 - 1e-6)
     float theta2;    // multipole split: theta^2 (0: no split)
+    float gt2;       //   and theta^2 (2 r_s^2)^2 (the Gaussian length of the kernel)
     float rc2far;    // FP32 at most r_c^2 (1 - 1e-6): a far pair lies wholly inside the cutoff
 };
 
@@ -476,6 +477,76 @@ __global__ void k_leaf_fill(const int64_t* __restrict__ flag, const int64_t* __r
     lkey[g] = cell_prefix(key[i], level[i]);
 }
 
+// Leaf packing (the host builder's rule): consecutive sibling leaves (the
+// same level L >= 1 and the same parent cell; chunks of an over-full finest
+// cell excluded) share one leaf while their total stays within max_leaf,
+// taken greedily in Morton order.  A pack of several leaves takes the
+// parent's cell (its level; its key stays that of its first member, whose
+// top bits name the parent), a pack of one keeps its own.  The first leaf of each run of
+// siblings (at most 8) packs the run: pstart[g] = 1 where a pack begins,
+// psize[g] = the leaves of the pack that begins at g.
+__device__ __forceinline__ bool packable(const int32_t* __restrict__ llevel,
+                                         const uint64_t* __restrict__ lkey, int64_t nl, int64_t g)
+{
+    const int L = llevel[g];
+    if (L < 1) return false;
+    if (L == kMortonBits)  // a chunk of an over-full finest cell shares its key with a neighbour
+        return !((g > 0 && llevel[g - 1] == L && lkey[g - 1] == lkey[g]) ||
+                 (g + 1 < nl && llevel[g + 1] == L && lkey[g + 1] == lkey[g]));
+    return true;
+}
+
+__device__ __forceinline__ bool siblings(const int32_t* __restrict__ llevel,
+                                         const uint64_t* __restrict__ lkey, int64_t nl, int64_t g)
+{
+    const int L = llevel[g];
+    return g > 0 && llevel[g - 1] == L && packable(llevel, lkey, nl, g - 1) &&
+           packable(llevel, lkey, nl, g) &&
+           cell_prefix(lkey[g - 1], L - 1) == cell_prefix(lkey[g], L - 1);
+}
+
+__global__ void k_pack_mark(const int32_t* __restrict__ lfirst, const int32_t* __restrict__ llevel,
+                            const uint64_t* __restrict__ lkey, int64_t nl, int max_leaf,
+                            int64_t* __restrict__ pstart, int32_t* __restrict__ psize)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nl || siblings(llevel, lkey, nl, g)) return;  // not the first of its run
+    int64_t start = g;
+    int cnt = 0, k = 0;
+    for (int64_t j = g; j < nl && (j == g || siblings(llevel, lkey, nl, j)); ++j) {
+        const int c = lfirst[j + 1] - lfirst[j];
+        if (j == g || cnt + c > max_leaf) {
+            if (j > g) psize[start] = k;
+            pstart[j] = 1;
+            start = j;
+            cnt = c;
+            k = 1;
+        } else {
+            pstart[j] = 0;
+            cnt += c;
+            ++k;
+        }
+    }
+    psize[start] = k;
+}
+
+__global__ void k_pack_fill(const int64_t* __restrict__ pstart, const int64_t* __restrict__ pid,
+                            const int32_t* __restrict__ psize, const int32_t* __restrict__ lfirst,
+                            const int32_t* __restrict__ llevel, const uint64_t* __restrict__ lkey,
+                            int64_t nl, int32_t* __restrict__ lfirst2, int32_t* __restrict__ llevel2,
+                            uint64_t* __restrict__ lkey2)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g == nl - 1) lfirst2[pid[g] + pstart[g]] = lfirst[nl];  // lfirst[packs] = n
+    if (g >= nl || !pstart[g]) return;
+    const int64_t p = pid[g];
+    const bool multi = psize[g] > 1;
+    lfirst2[p] = lfirst[g];
+    llevel2[p] = multi ? llevel[g] - 1 : llevel[g];
+    lkey2[p] = lkey[g];  // the first member's key keeps the keys sorted (an earlier,
+                         // deeper sibling subtree can hold keys above the parent's prefix)
+}
+
 __global__ void k_leaf_box(const int32_t* __restrict__ lfirst, int64_t nl, int64_t n,
                            const double* __restrict__ wpos, const int32_t* __restrict__ idx,
                            double* __restrict__ lbox, float4* __restrict__ lrec,
@@ -695,13 +766,17 @@ __device__ __forceinline__ float maxgap2_upper(const float* alo, const float* ah
 // rounded outward, against r_c^2 (1 - 1e-6) rounded down: the cutoff then
 // removes no pair the expansion includes) and the box centres are R apart
 // with theta |R| >= rho_I + rho_J (rho: half the diagonal of the outward
-// box; an opening test, in FP32 with explicit roundings so that the count
-// and the write pass decide alike).  alo/ahi, ra: box I and its rho; b0 =
-// (lo of box J), b1 = (hi of box J, rho_J); sd/su: the shift rounded down
-// and up.
+// box), and, with PSR_BUILD_SPLIT_GAUSSIAN, also theta 2 r_s^2 / |R| >=
+// rho_I + rho_J: 2 r_s^2 / |R| is the length on which the kernel's Gaussian
+// truncation varies (d/dR of -R^2 / 4 r_s^2), shorter than |R| beyond
+// r = sqrt(2) r_s (gt2 = theta^2 (2 r_s^2)^2, or infinity without the flag).
+// The opening test is taken in FP32 with explicit roundings so that the
+// count and the write pass decide alike.
+// alo/ahi, ra: box I and its rho; b0 = (lo of box J), b1 = (hi of box J,
+// rho_J); sd/su: the shift rounded down and up.
 __device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, float ra, float4 b0,
                                          float4 b1, const float* sd, const float* su,
-                                         float theta2, float rc2far)
+                                         float theta2, float gt2, float rc2far)
 {
     const float blo[3] = {b0.x, b0.y, b0.z}, bhi[3] = {b1.x, b1.y, b1.z};
     float m2 = 0.f, d2 = 0.f;
@@ -715,7 +790,8 @@ __device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, flo
         d2 = __fmaf_rn(d, d, d2);
     }
     const float r = __fadd_rn(ra, b1.w);
-    return d2 > 0.f && m2 < rc2far && __fmul_rn(theta2, d2) >= __fmul_rn(r, r);
+    const float r2 = __fmul_rn(r, r);
+    return d2 > 0.f && m2 < rc2far && __fmul_rn(theta2, d2) >= r2 && __fmul_rn(r2, d2) <= gt2;
 }
 
 // One thread per target leaf.  WRITE = false counts the row and its work;
@@ -1044,7 +1120,7 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
                 const float4 b0 = sbox[wp][owner][0], b1 = sbox[wp][owner][1];
                 const float alo[3] = {b0.x, b0.y, b0.z}, ahi[3] = {b1.x, b1.y, b1.z};
                 far = far_pair(alo, ahi, b1.w, lout[2 * (int64_t)J], lout[2 * (int64_t)J + 1],
-                               fd, fu, bx.theta2, bx.rc2far);
+                               fd, fu, bx.theta2, bx.gt2, bx.rc2far);
                 if (!WRITE && !far) nsrc = lfirst[J + 1] - lfirst[J];
             }
             const unsigned seg = __match_any_sync(kFull, owner);
@@ -1219,6 +1295,7 @@ BoxK box_k(const psr_box& b)
     k.thi = float_at_least(k.rc2m * (1.0 + 1e-6));
     k.tlo = float_at_most(k.rc2m * (1.0 - 1e-6));
     k.theta2 = 0.0f;
+    k.gt2 = 0.0f;
     k.rc2far = float_at_most(b.r_c * b.r_c * (1.0 - 1e-6));
     return k;
 }
@@ -1252,8 +1329,9 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     if (!d_pos || !box || n < 1 || n > kMaxN)
         return dfail(PSR_E_ARG, "null argument or n outside [1, 2^28]");
     if (max_leaf < 1 || max_leaf > kMaxLeaf) return dfail(PSR_E_ARG, "max_leaf must be in [1, 64]");
-    if (flags & ~PSR_BUILD_NO_FP64)
-        return dfail(PSR_E_ARG, "the device builder takes PSR_BUILD_NO_FP64 only (no ORB)");
+    if (flags & ~(PSR_BUILD_NO_FP64 | PSR_BUILD_UNPACKED | PSR_BUILD_SPLIT_GAUSSIAN))
+        return dfail(PSR_E_ARG, "the device builder takes PSR_BUILD_NO_FP64, PSR_BUILD_UNPACKED "
+                                "and PSR_BUILD_SPLIT_GAUSSIAN (no ORB)");
     if (!(std::isfinite(box->L) && box->L > 0) || !(std::isfinite(box->r_s) && box->r_s > 0) ||
         !std::isfinite(box->G))
         return dfail(PSR_E_ARG, "L, r_s must be finite and positive");
@@ -1294,6 +1372,8 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     long long* cnt = (long long*)(s + S.cnt);
     BoxK bx = box_k(*box);
     bx.theta2 = (float)(theta * theta);
+    bx.gt2 = (flags & PSR_BUILD_SPLIT_GAUSSIAN) ? (float)(theta * theta * 4.0 * std::pow(box->r_s, 4))
+                                               : INFINITY;
 
     int e;
     if ((e = (int)cudaMemsetAsync(cnt, 0, 8 * kCntWords, st))) return dcuda(e, "cudaMemsetAsync");
@@ -1312,6 +1392,30 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 1) return dfail(PSR_E_ARG, "non-finite position or mass");
     if (nl < 1 || nl > n || nl >= (1 << 27)) return dfail(PSR_E_ARG, "leaf count out of range");
+    if (!(flags & PSR_BUILD_UNPACKED)) {
+        // pack sibling leaves: marks, pack ids, packed arrays in the (still
+        // free) tree regions, copied back over the leaf arrays
+        int64_t* pstart = flag;
+        int64_t* pid = lid;
+        int32_t* psize = tflag;
+        int32_t* lfirst2 = (int32_t*)tspan;
+        int32_t* llevel2 = tpari;
+        uint64_t* lkey2 = (uint64_t*)tnode;
+        k_pack_mark<<<nblk(nl, 256), 256, 0, st>>>(lfirst, llevel, lkey, nl, max_leaf, pstart, psize);
+        if ((e = (int)cudaGetLastError())) return dcuda(e, "leaf packing kernel");
+        if ((e = scan_exclusive(pstart, pid, nl, tiles, total, st))) return dcuda(e, "scan");
+        k_pack_fill<<<nblk(nl, 256), 256, 0, st>>>(pstart, pid, psize, lfirst, llevel, lkey, nl,
+                                                   lfirst2, llevel2, lkey2);
+        if ((e = (int)cudaGetLastError())) return dcuda(e, "leaf packing kernel");
+        int64_t np = 0;
+        if ((e = read_back(&np, total, 8, st, timeout_ms))) return e;
+        if (np < 1 || np > nl) return dfail(PSR_E_DEVICE, "leaf packing failed");
+        if ((e = (int)cudaMemcpyAsync(lfirst, lfirst2, 4 * (np + 1), cudaMemcpyDeviceToDevice, st)) ||
+            (e = (int)cudaMemcpyAsync(llevel, llevel2, 4 * np, cudaMemcpyDeviceToDevice, st)) ||
+            (e = (int)cudaMemcpyAsync(lkey, lkey2, 8 * np, cudaMemcpyDeviceToDevice, st)))
+            return dcuda(e, "cudaMemcpyAsync");
+        nl = np;
+    }
     k_leaf_box<<<nblk(nl, 256), 256, 0, st>>>(lfirst, nl, n, wpos, v0, lbox, lrec,
                                               (float4*)(s + S.lout), cnt);
     if (nl >= 2) {
@@ -1441,6 +1545,9 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
     if (h->has_far) {
         BoxK bxw = bx;
         bxw.theta2 = (float)(h->theta * h->theta);
+        bxw.gt2 = (h->flags & PSR_BUILD_SPLIT_GAUSSIAN)
+                      ? (float)(h->theta * h->theta * 4.0 * std::pow(h->boxes[0].r_s, 4))
+                      : INFINITY;
         k_pairs_split<true><<<nblk(nl, 128), 128, 0, st>>>(
             nl, bxw, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.lout),
             (const float4*)(s + S.nodef), rootbox, nullptr, nullptr, nullptr, rowptr,

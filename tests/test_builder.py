@@ -431,7 +431,7 @@ def test_build_flag_checks():
     with pytest.raises(psr.PsrError) as e:
         capi.psr_build_leaves(np.ascontiguousarray(b.pos).ctypes.data_as(
             __import__("ctypes").POINTER(__import__("ctypes").c_double)), None, b.n,
-            capi.psr_box(b.L, b.r_s, b.r_c, 1.0), 32, 4)
+            capi.psr_box(b.L, b.r_s, b.r_c, 1.0), 32, 8)
     assert e.value.code == capi.PSR_E_ARG
     box = capi.psr_box(10.0, 0.5, 2.25, 1.0)
     fake = 1 << 40  # never dereferenced: the flag check fails first
@@ -439,3 +439,52 @@ def test_build_flag_checks():
         capi.psr_device_build(fake, 0, 100, box, 32, capi.PSR_BUILD_ORB, fake,
                               capi.psr_device_build_scratch_bytes(100), 0, 1000)
     assert e.value.code == capi.PSR_E_ARG
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("max_leaf", [1, 8, 32])
+def test_leaf_packing_merges_consecutive_siblings(case, max_leaf):
+    """Default (packed) leaves against PSR_BUILD_UNPACKED on the same input:
+    the same particle order; every packed leaf is a run of consecutive
+    unpacked leaves of one level L and one parent cell, with the parent's
+    cell (level L - 1) when the run has several; runs are greedy: the next
+    sibling starts a new pack only when it would take the pack past
+    max_leaf."""
+    b = CASES[case]()
+    pk = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf)
+    up = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf, pack=False)
+    assert np.array_equal(pk.perm, up.perm)
+    P, U = pk.host_arrays(), up.host_arrays()
+    ustart = {int(f): i for i, f in enumerate(U["leaf"][:, 0])}
+    step = lambda lvl: 2 ** (21 - lvl)
+    parent = lambda lc: tuple((lc[:3] // (2 * step(lc[3] - 1))).tolist()) + (int(lc[3]) - 1,)
+    for g in range(P["leaf"].shape[0]):
+        f, c = int(P["leaf"][g, 0]), int(P["leaf"][g, 1])
+        i = ustart[f]  # packs start on an unpacked leaf boundary
+        j, tot = i, 0
+        while tot < c:
+            tot += int(U["leaf"][j, 1])
+            j += 1
+        assert tot == c
+        run = U["lcen"][i:j]
+        if j - i == 1:
+            assert np.array_equal(P["lcen"][g], run[0])
+            continue
+        assert np.all(run[:, 3] == run[0, 3]) and run[0, 3] >= 1
+        assert len({parent(r) for r in run}) == 1
+        lv = run[0, 3] - 1
+        expect = (np.array(parent(run[0])[:3]) * 2 + 1) * step(lv)
+        assert np.array_equal(P["lcen"][g, :3], expect) and P["lcen"][g, 3] == lv
+    # greedy: a pack followed by an unpacked sibling of the same parent ends
+    # only because that sibling would not fit
+    for g in range(P["leaf"].shape[0] - 1):
+        f2 = int(P["leaf"][g + 1, 0])
+        nxt = ustart[f2]
+        prev = nxt - 1
+        a, b_ = U["lcen"][prev], U["lcen"][nxt]
+        if a[3] == b_[3] and a[3] >= 1 and parent(a) == parent(b_) and \
+                int(U["leaf"][nxt, 1]) <= max_leaf:
+            # same parent, both plain leaves: the split must be forced by size
+            # (or by an over-full finest cell's chunks, which never pack)
+            chunk = a[3] == 21 and np.array_equal(a[:3], b_[:3])
+            assert chunk or int(P["leaf"][g, 1]) + int(U["leaf"][nxt, 1]) > max_leaf

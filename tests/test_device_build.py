@@ -211,3 +211,18 @@ def test_device_build_on_a_side_stream_and_sharded_launch():
     assert np.array_equal(full.cpu().numpy(), host.forces(psr.Options()).cpu().numpy())
     t0 = gpu.shard_targets(3, 0)
     assert np.array_equal(t0, host.shard_targets(3, 0))
+
+
+@pytest.mark.parametrize("case", ["clustered", "coincident", "lattice_cutoff8", "nfw64"])
+def test_device_build_unpacked_equals_host_unpacked(case):
+    """PSR_BUILD_UNPACKED on both builders: plain octree leaves, bit for bit."""
+    b = CASES[case]()
+    dev = torch.device("cuda")
+    host = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf, pack=False)
+    host.upload(dev)
+    pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
+    mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
+    gpu = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, b.max_leaf, pack=False)
+    _compare(host, gpu)
+    packed = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf)
+    assert packed.info.n_leaves <= host.info.n_leaves

@@ -55,13 +55,13 @@ CASES = {
 }
 
 
-def _builds(b, theta, fp64=True):
+def _builds(b, theta, fp64=True, gaussian=False):
     dev = torch.device("cuda")
     pos = torch.tensor(b.pos, dtype=torch.float64, device=dev)
     mass = torch.tensor(b.mass, dtype=torch.float64, device=dev)
     full = psr.Leaves.device_build(pos, mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf, fp64=fp64)
     split = psr.Leaves.device_build(pos, mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf, fp64=fp64,
-                                    theta=theta)
+                                    theta=theta, gaussian_mac=gaussian)
     return full, split
 
 
@@ -83,9 +83,10 @@ def _rows(rowptr, pairs):
     return I, (pairs >> 5).astype(np.int64), (pairs & 31).astype(np.int64)
 
 
-def _accept(lo, hi, I, J, code, L, theta, r_c):
+def _accept(lo, hi, I, J, code, L, theta, r_c, r_s, gaussian):
     """The split's test in FP64: (largest point-pair distance^2 / r_c^2,
-    theta^2 |R|^2 / (rho_I + rho_J)^2, |R|^2)."""
+    theta^2 l^2 / (rho_I + rho_J)^2, |R|^2), l = |R|, or with the Gaussian
+    term min(|R|, 2 r_s^2 / |R|)."""
     sh = _shifts(code, L)
     d2 = m2 = ra2 = rb2 = np.zeros(len(I))
     for a in range(3):
@@ -97,15 +98,17 @@ def _accept(lo, hi, I, J, code, L, theta, r_c):
         ra2, rb2 = ra2 + ea * ea, rb2 + eb * eb
     s2 = (np.sqrt(ra2) + np.sqrt(rb2)) ** 2
     with np.errstate(divide="ignore", invalid="ignore"):
-        mac = np.where(s2 > 0, theta * theta * d2 / s2, np.inf)
+        scale2 = np.minimum(d2, (2 * r_s * r_s) ** 2 / d2) if gaussian else d2
+        mac = np.where(s2 > 0, theta * theta * scale2 / s2, np.inf)
     return m2 / (r_c * r_c), mac, d2
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("theta", [0.4, 0.7])
-def test_split_partitions_the_pair_list_by_the_acceptance_test(case, theta):
+@pytest.mark.parametrize("gaussian", [False, True])
+def test_split_partitions_the_pair_list_by_the_acceptance_test(case, theta, gaussian):
     b = CASES[case]()
-    full, split = _builds(b, theta)
+    full, split = _builds(b, theta, gaussian=gaussian)
     full.check()
     split.check()
     fi, si = full.info, split.info
@@ -124,11 +127,11 @@ def test_split_partitions_the_pair_list_by_the_acceptance_test(case, theta):
     # each side is the acceptance test
     lo, hi = _leaf_boxes(DS)
     I, J, code = _rows(F["frow"], F["fpairs"])
-    inside, mac, d2 = _accept(lo, hi, I, J, code, b.L, theta, b.r_c)
+    inside, mac, d2 = _accept(lo, hi, I, J, code, b.L, theta, b.r_c, b.r_s, gaussian)
     assert np.all(inside < 1.0) and np.all(d2 > 0)
     assert np.all(mac >= 1.0 - 1e-5)
     I, J, code = _rows(DS["rowptr"], DS["pairs"])
-    inside, mac, d2 = _accept(lo, hi, I, J, code, b.L, theta, b.r_c)
+    inside, mac, d2 = _accept(lo, hi, I, J, code, b.L, theta, b.r_c, b.r_s, gaussian)
     far_by_margin = (inside < 1.0 - 1e-4) & (mac > 1.0 + 1e-4) & (d2 > 0)
     assert not far_by_margin.any(), np.flatnonzero(far_by_margin)[:10]
     # expansion centres
@@ -140,7 +143,7 @@ def test_split_partitions_the_pair_list_by_the_acceptance_test(case, theta):
     unit = b.L / 2.0 ** 22
     back = DS["lcen"][:, :3].astype(np.float64) * unit + F["fofs"][:, :3].astype(np.float64)
     assert np.allclose(back, F["fcen"][:, :3], rtol=0, atol=4e-7 * b.L)
-    if case != "small_box":
+    if case.startswith("clustered") and not gaussian:  # dense halos: small, well separated leaves
         assert si.n_far > 0
 
 
@@ -162,7 +165,7 @@ def _far_direct(b, DS, F, rows):
     return out
 
 
-@pytest.mark.parametrize("case", ["clustered", "uniform32"])
+@pytest.mark.parametrize("case", ["clustered", "clustered_leaf8"])
 def test_fmm_forces_far_part_converges_to_the_direct_sum(case):
     """Relative RMS error of the far part over sampled target leaves, below
     2 theta^(p+1) / (1 - theta) (the order-p remainder of a pair whose radii
