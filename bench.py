@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--fmm-order", type=int, default=4)
     p.add_argument("--split-steps", type=int, default=3,
                    help="timed steps of the split short range (P2P near + multipole far)")
-    p.add_argument("--split-theta", type=float, default=0.5)
+    p.add_argument("--split-theta", default="0.5,0.7",
+                   help="opening parameters of the split (the first also with the Gaussian term)")
     p.add_argument("--split-orders", default="4,6")
     p.add_argument("--paper-steps", type=int, default=3,
                    help="timed steps of each prior-art variant (the paper's block-per-leaf "
@@ -327,14 +328,14 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
     oracle comparison."""
     pos_d = torch.tensor(b.pos, dtype=torch.float64, device=dev)
     mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
-    theta = args.split_theta
+    thetas = [float(x) for x in str(args.split_theta).split(",") if x]
     orders = [int(x) for x in args.split_orders.split(",") if x]
-    out = {"theta": theta, "full_p2p_ms": full_ms, "evaluated_full": int(full_evaluated),
-           "rules": []}
+    out = {"full_p2p_ms": full_ms, "evaluated_full": int(full_evaluated), "rules": []}
     totals = {}
-    for rule, gauss in (("theta |R| >= rho_I + rho_J, both boxes wholly within r_c", False),
-                        ("theta min(|R|, 2 r_s^2/|R|) >= rho_I + rho_J, both boxes wholly "
-                         "within r_c", True)):
+    runs = [(t, "theta |R| >= rho_I + rho_J, both boxes wholly within r_c", False) for t in thetas]
+    runs.append((thetas[0], "theta min(|R|, 2 r_s^2/|R|) >= rho_I + rho_J, both boxes wholly "
+                            "within r_c", True))
+    for theta, rule, gauss in runs:
         mk = lambda: psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G,
                                              max_leaf=b.max_leaf, theta=theta, gaussian_mac=gauss)
         lv = mk()
@@ -351,7 +352,7 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
         nl = int(inf.n_leaves)
         scratch = torch.empty(2 * nl * ((capi_ncoef(max(orders)) + 3) // 4 * 4),
                               dtype=torch.float32, device=dev)
-        r = {"acceptance": rule, "leaves": nl, "near_entries": int(inf.n_pairs),
+        r = {"theta": theta, "acceptance": rule, "leaves": nl, "near_entries": int(inf.n_pairs),
              "far_entries": int(inf.n_far), "evaluated_near": int(inf.evaluated_pairs),
              "p2p_interactions_moved_to_m2l": 1.0 - inf.evaluated_pairs / full_evaluated,
              "device_build_split_ms": build_ms, "orders": []}
@@ -377,12 +378,12 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
             tn /= args.split_steps
             tf /= args.split_steps
             lv.check()
-            totals[(gauss, p)] = acc.double().cpu().numpy()
+            totals[(theta, gauss, p)] = acc.double().cpu().numpy()
             r["orders"].append({"order": p, "p2p_near_ms": tn, "fmm_far_ms": tf,
                                 "short_range_ms": tn + tf,
                                 "speedup_vs_full_p2p": full_ms / (tn + tf),
                                 "m2l_entries_per_s_upper_bound_time": inf.n_far / (tf / 1e3),
-                                "status": int(status.item()), "_key": [gauss, p]})
+                                "status": int(status.item()), "_key": [theta, gauss, p]})
         out["rules"].append(r)
         del lv
     return out, totals
