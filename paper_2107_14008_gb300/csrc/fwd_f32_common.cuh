@@ -508,6 +508,22 @@ __device__ __forceinline__ bool prefer_two_per_lane(int n)
     return e2 > 2 * e1 + (2 * e1) / 16;  // > 6 % better
 }
 
+// Targets per lane for the scalar kernel: 3 where it fills clearly more lane
+// slots than 1 or 2 (leaves of 17-18 and 21-24 particles: 24 = 8 lanes x 3
+// targets x 4 streams), else the choice above.  Three target slots need
+// 3 x 768 B of the warp's staging buffer for the final reduction, so only
+// with tiles of at least 128 particles.
+__device__ __forceinline__ int targets_per_lane(int n, int cap)
+{
+    const int two = prefer_two_per_lane(n) ? 2 : 1;
+    if (n > 32 || cap < 128) return two;
+    const int t3 = (n + 2) / 3;
+    const int e3 = n * (32 / t3);                               // x 1/96
+    const int eb = two == 2 ? n * (32 / ((n + 1) >> 1)) : n * (32 / n);  // x 1/64 or 1/32
+    const int eb96 = two == 2 ? eb * 3 / 2 : eb * 3;            // x 1/96
+    return e3 > eb96 + eb96 / 16 ? 3 : two;                     // > 6 % better
+}
+
 // Shared memory: the table, then one staging buffer of stage_cap particles
 // plus 32 entry records per warp.
 template <int TM, int ACC, bool COUNT, bool WIDE, bool PK>
@@ -563,7 +579,10 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
             else
                 fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
         } else {
-            if (WIDE && prefer_two_per_lane(li.y))
+            const int R = WIDE ? targets_per_lane(li.y, a.stage_cap) : 1;
+            if (R == 3)
+                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs);
+            else if (R == 2)
                 fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs);
             else
                 fwd_item_sc<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
