@@ -56,11 +56,17 @@ extern "C" {
 
 /* ------------------------------------------------------------ options */
 /* precision of the pair arithmetic */
-#define PSR_FP64 0        /* FP64 throughout, T from erfc/exp               */
+#define PSR_FP64 0        /* FP64 throughout, T from erfc/exp; with interp
+                             PSR_TAYLOR2/4 the paper's double-precision table
+                             path instead (Section 3.3: the Taylor table in
+                             FP64 about the nearest node, 1/r by Newton-
+                             Raphson from an FP32 estimate; forward only, not
+                             in psr_p2p_forces_noalloc)                     */
 #define PSR_FP32_EXACT 1  /* FP32 pair math, T from erfcf/expf              */
 #define PSR_FP32_TABLE 2  /* FP32 pair math, T interpolated from a table
                              in shared memory (Section 3.3)                 */
-/* interpolation of the table (PSR_FP32_TABLE) */
+/* interpolation of the table (PSR_FP32_TABLE; the Taylor levels also
+   select PSR_FP64's table path) */
 #define PSR_LINEAR 0      /* chord between nodes                            */
 #define PSR_CUBIC 1       /* cubic Hermite on (T_k, T'_k = x_k^2 E_k)       */
 #define PSR_TAYLOR2 2     /* the paper's Taylor table (Section 3.3, Eq. int)

@@ -150,14 +150,21 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     return a;
 }
 
+bool fp64_taylor(const Opts& o)
+{
+    return o.precision == PSR_FP64 && (o.interp == PSR_TAYLOR2 || o.interp == PSR_TAYLOR4);
+}
+
 int ensure_table(Leaves* h, const Opts& o, cudaStream_t st)
 {
-    if (o.precision != PSR_FP32_TABLE) return PSR_OK;
+    const bool t64 = fp64_taylor(o);
+    if (o.precision != PSR_FP32_TABLE && !t64) return PSR_OK;
     const double x_c = h->boxes[0].r_c / (2.0 * h->boxes[0].r_s);
-    int key = o.table_n * 4 + o.interp;
+    int key = (o.table_n * 4 + o.interp) * 2 + (t64 ? 1 : 0);
     if (key == h->table_key && x_c == h->table_xc) return PSR_OK;
     char* t = h->d_ws + h->lay.table;
-    int e = launch_table(o.table_n, o.interp, x_c, t, t + (size_t)(kMaxTableN + 1) * 16, st);
+    int e = t64 ? launch_table64(o.table_n, o.interp, x_c, t, st)
+                : launch_table(o.table_n, o.interp, x_c, t, t + (size_t)(kMaxTableN + 1) * 16, st);
     if (e) return cuda_fail((cudaError_t)e, "table kernel launch");
     h->table_key = key;
     h->table_xc = x_c;
@@ -173,7 +180,7 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
             e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
                               o.tile ? o.tile : kAdjStageCap, &occ);
         else if (o.precision == PSR_FP64)
-            e = fwd_f64_occupancy(o.warps, h->max_leaf, &occ);
+            e = fwd_f64_occupancy(o.warps, h->max_leaf, o.interp, o.table_n, &occ);
         else if (o.kernel == PSR_KERNEL_PAPER)
             e = fwd_blk_occupancy(o.precision, o.interp, o.accum, h->max_leaf, o.table_n, &occ);
         else {
@@ -359,6 +366,8 @@ int psr_p2p_adjoint(psr_leaves* hh, const psr_opts* opts, const void* d_cot, voi
     if (rc) return rc;
     if (o.precision == PSR_FP32_TABLE && o.interp != PSR_LINEAR && o.interp != PSR_CUBIC)
         return fail(PSR_E_ARG, "the adjoint takes PSR_LINEAR or PSR_CUBIC tables");
+    if (fp64_taylor(o))
+        return fail(PSR_E_ARG, "the FP64 Taylor table path is forward-only (the FP64 adjoint is plain)");
     if (h->n == 0) return PSR_OK;  // nothing to compute
     if (o.precision == PSR_FP64 && !h->has_pd)
         return fail(PSR_E_STATE, "built with PSR_BUILD_NO_FP64: no FP64 payload");

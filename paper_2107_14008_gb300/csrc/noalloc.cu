@@ -85,6 +85,11 @@ extern "C" int psr_p2p_forces_noalloc(psr_leaves* hh, const psr_opts* opts, void
     int precision = 0;
     int rc = prepare_forward(h, opts, &a, &precision);
     if (rc) return rc;
+    if (precision == PSR_FP64 && (a.interp == PSR_TAYLOR2 || a.interp == PSR_TAYLOR4)) {
+        set_last_error("psr_p2p_forces_noalloc: the FP64 Taylor table path needs the workspace's "
+                       "table (use psr_p2p_forces)");
+        return PSR_E_ARG;
+    }
     if (precision == PSR_FP32_TABLE &&
         (size_t)(a.table_n + 1) * (a.interp == PSR_LINEAR || a.interp == PSR_CUBIC ? 16 : 32) >
             kTableBytes) {

@@ -1,5 +1,9 @@
 // FP64 forward P2P kernel: the plain double-precision path (paper, Section 2
-// pair force with Eq. tr evaluated by erfc/exp, Section 3.2 kernel layout).
+// pair force with Eq. tr evaluated by erfc/exp, Section 3.2 kernel layout),
+// or, with a Taylor interpolation level, the paper's double-precision table
+// path (Section 3.3: the Eq. int expansion about the nearest of N + 1 nodes,
+// level T_[4] for double precision) with the table in shared memory and
+// 1/r from an FP32 estimate refined by two Newton-Raphson steps in FP64.
 // Same work decomposition as the FP32 kernels (warp per target leaf, S
 // streams of T lanes, persistent ticket); coordinates are the wrapped FP64
 // positions and each leaf pair adds its periodic image n L exactly as the
@@ -10,8 +14,46 @@
 
 namespace psr {
 
-template <bool COUNT, int R>
-__device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li,
+// Taylor table in FP64: node k = 0..N, x_k = k h, h = x_c / N; six doubles
+// per node, the Eq. int coefficients of eps^m (eps = x - x_k) times h^m, so
+// that the expansion is a polynomial in f = x/h - k (zero above the level).
+__global__ void table64_kernel(int N, int level, double x_c, double* __restrict__ t)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > N) return;
+    const double h = x_c / N, x = k * h, x2 = x * x;
+    const double E = -2.0 * 1.1283791670955126 * exp(-x2);  // -4 exp(-x^2) / sqrt(pi)
+    double* c = t + 6 * (int64_t)k;
+    c[0] = erfc(x) - 0.5 * x * E;
+    c[1] = x2 * E * h;
+    c[2] = -x * (x2 - 1.0) * E * h * h;
+    c[3] = level >= 4 ? (2.0 / 3.0 * x2 * x2 - 5.0 / 3.0 * x2 + 1.0 / 3.0) * E * h * h * h : 0.0;
+    c[4] = level >= 4 ? -x * (x2 * x2 / 3.0 - 1.5 * x2 + 1.0) * E * h * h * h * h : 0.0;
+    c[5] = 0.0;
+}
+
+int launch_table64(int table_n, int interp, double x_c, void* d_out, void* stream)
+{
+    const int threads = 256, blocks = (table_n + 1 + threads - 1) / threads;
+    table64_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(
+        table_n, interp == PSR_TAYLOR4 ? 4 : 2, x_c, reinterpret_cast<double*>(d_out));
+    return (int)cudaGetLastError();
+}
+
+// 1/sqrt(r2) for r2 > 0: an FP32 estimate (FP64 rsqrt where r2 leaves the
+// FP32 normal range) refined by two Newton-Raphson steps for 1/sqrt,
+// y <- y (3 - r2 y^2) / 2, each of which squares the relative error.
+__device__ __forceinline__ double rsqrt_nr(double r2)
+{
+    const float f = (float)r2;
+    double y = (f > 1e-36f && f < 1e36f) ? (double)rsqrtf(f) : rsqrt(r2);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    return y;
+}
+
+template <bool COUNT, int R, bool TAYLOR>
+__device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li, const double* tab,
                                            unsigned long long& npairs)
 {
     const int lane = threadIdx.x & 31;
@@ -25,6 +67,8 @@ __device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li,
     const BoxDev& bx = a.boxes[li.z];
     const double L = bx.L, rc2 = bx.rc2, inv2rs = bx.inv_2rs;
     const double c2 = 1.1283791670955126;  // 2 / sqrt(pi)
+    const double nmax = (double)a.table_n;
+    const double uscale = nmax / bx.r_c;  // r -> x N / x_c (table units), in FP64
 
     double4 xi[R];
     bool act[R];
@@ -80,10 +124,21 @@ __device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li,
             double dx = p.x - tx[r], dy = p.y - ty[r], dz = p.z - tz[r];
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < rc2 && r2 > 0.0) {
-                double rr = sqrt(r2);
-                double x = rr * inv2rs;
-                double T = erfc(x) + c2 * x * exp(-x * x);
-                double w = p.w * T / (r2 * rr);
+                double w;
+                if (TAYLOR) {
+                    const double ri = rsqrt_nr(r2);
+                    const double u = r2 * ri * uscale;
+                    const double kf = fmin(rint(u), nmax);
+                    const double f = u - kf;
+                    const double* c = tab + 6 * (int)kf;
+                    const double T = fma(f, fma(f, fma(f, fma(f, c[4], c[3]), c[2]), c[1]), c[0]);
+                    w = p.w * T * ri * ri * ri;
+                } else {
+                    double rr = sqrt(r2);
+                    double x = rr * inv2rs;
+                    double T = erfc(x) + c2 * x * exp(-x * x);
+                    w = p.w * T / (r2 * rr);
+                }
                 ax[r] += w * dx;
                 ay[r] += w * dy;
                 az[r] += w * dz;
@@ -112,9 +167,17 @@ __device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li,
     }
 }
 
-template <bool COUNT, bool WIDE>
+template <bool COUNT, bool WIDE, bool TAYLOR>
 __global__ void __launch_bounds__(256) p2p_fwd_f64_kernel(const FwdArgs a)
 {
+    extern __shared__ __align__(16) unsigned char smem64[];
+    const double* tab = reinterpret_cast<const double*>(smem64);
+    if (TAYLOR) {
+        const double* g = reinterpret_cast<const double*>(a.table);
+        for (int i = threadIdx.x; i < 6 * (a.table_n + 1); i += blockDim.x)
+            reinterpret_cast<double*>(smem64)[i] = g[i];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     unsigned long long npairs = 0;
@@ -135,9 +198,9 @@ __global__ void __launch_bounds__(256) p2p_fwd_f64_kernel(const FwdArgs a)
             continue;
         }
         if (WIDE && li.y > 32)
-            fwd64_item<COUNT, 2>(a, I, li, npairs);
+            fwd64_item<COUNT, 2, TAYLOR>(a, I, li, tab, npairs);
         else
-            fwd64_item<COUNT, 1>(a, I, li, npairs);
+            fwd64_item<COUNT, 1, TAYLOR>(a, I, li, tab, npairs);
     }
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) npairs += __shfl_xor_sync(kFull, npairs, off);
@@ -147,25 +210,59 @@ __global__ void __launch_bounds__(256) p2p_fwd_f64_kernel(const FwdArgs a)
     persistent_exit(a.ctrl + kCtrlTicketFwd, a.ctrl + kCtrlDoneFwd);
 }
 
-int launch_fwd_f64(const FwdArgs& a, void* stream)
+namespace {
+
+bool taylor64(int interp) { return interp == PSR_TAYLOR2 || interp == PSR_TAYLOR4; }
+
+template <bool COUNT, bool WIDE, bool TAYLOR>
+int launch64(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    bool wide = a.max_leaf > 32;
-    if (a.count_pairs) {
-        if (wide) p2p_fwd_f64_kernel<true, true><<<a.blocks, a.warps_per_block * 32, 0, st>>>(a);
-        else p2p_fwd_f64_kernel<true, false><<<a.blocks, a.warps_per_block * 32, 0, st>>>(a);
-    } else {
-        if (wide) p2p_fwd_f64_kernel<false, true><<<a.blocks, a.warps_per_block * 32, 0, st>>>(a);
-        else p2p_fwd_f64_kernel<false, false><<<a.blocks, a.warps_per_block * 32, 0, st>>>(a);
+    auto k = p2p_fwd_f64_kernel<COUNT, WIDE, TAYLOR>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
     }
+    k<<<a.blocks, a.warps_per_block * 32, smem, st>>>(a);
     return (int)cudaGetLastError();
 }
 
-int fwd_f64_occupancy(int warps, int max_leaf, int* out)
+template <bool TAYLOR>
+const void* ptr64(bool wide)
 {
-    const void* f = max_leaf > 32 ? (const void*)p2p_fwd_f64_kernel<false, true>
-                                  : (const void*)p2p_fwd_f64_kernel<false, false>;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, warps * 32, 0);
+    return wide ? (const void*)p2p_fwd_f64_kernel<false, true, TAYLOR>
+                : (const void*)p2p_fwd_f64_kernel<false, false, TAYLOR>;
+}
+
+}  // namespace
+
+size_t fwd_f64_smem(int interp, int table_n)
+{
+    return taylor64(interp) ? (size_t)(table_n + 1) * 48 : 0;
+}
+
+int launch_fwd_f64(const FwdArgs& a, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool wide = a.max_leaf > 32, tay = taylor64(a.interp);
+    const size_t smem = fwd_f64_smem(a.interp, a.table_n);
+    if (tay) {
+        if (a.count_pairs) return wide ? launch64<true, true, true>(a, smem, st) : launch64<true, false, true>(a, smem, st);
+        return wide ? launch64<false, true, true>(a, smem, st) : launch64<false, false, true>(a, smem, st);
+    }
+    if (a.count_pairs) return wide ? launch64<true, true, false>(a, 0, st) : launch64<true, false, false>(a, 0, st);
+    return wide ? launch64<false, true, false>(a, 0, st) : launch64<false, false, false>(a, 0, st);
+}
+
+int fwd_f64_occupancy(int warps, int max_leaf, int interp, int table_n, int* out)
+{
+    const bool wide = max_leaf > 32, tay = taylor64(interp);
+    const void* f = tay ? ptr64<true>(wide) : ptr64<false>(wide);
+    const size_t smem = fwd_f64_smem(interp, table_n);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, warps * 32, smem);
 }
 
 }  // namespace psr

@@ -175,7 +175,9 @@ int fwd_f32_occupancy(int precision, int interp, int accum, int warps, int max_l
                       int cap, int variant, int* out);
 size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap);
 constexpr size_t kSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block
-int fwd_f64_occupancy(int warps, int max_leaf, int* out);
+int fwd_f64_occupancy(int warps, int max_leaf, int interp, int table_n, int* out);
+int launch_table64(int table_n, int interp, double x_c, void* d_out, void* stream);  // p2p_fwd_f64.cu
+size_t fwd_f64_smem(int interp, int table_n);
 int launch_fwd_blk(const FwdArgs& a, int precision, void* stream);  // p2p_fwd_blk.cu
 int fwd_blk_occupancy(int precision, int interp, int accum, int max_leaf, int table_n, int* out);
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,

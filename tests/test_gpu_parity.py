@@ -593,3 +593,47 @@ def test_paper_kernel_sharded_and_graph_replayed():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out2.cpu().numpy(), whole)
     lv.check()
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "small_box"])
+@pytest.mark.parametrize("interp,level", TAYLOR)
+@pytest.mark.parametrize("table_n", [384, 1000])
+def test_fp64_taylor_table_matches_interpolated_oracle(case, interp, level, table_n):
+    """PSR_FP64 with a Taylor level: the paper's double-precision table path
+    (Section 3.3).  Against the oracle's Taylor mode (same nodes, level and
+    nearest node) only FP64 rounding remains; against the exact oracle the
+    level's truncation: T_[4] at the paper's spacing is below 1e-11, T_[2]
+    below 1e-7."""
+    b = CASES[case]()
+    ref, pairs, _ = oracle_acc(b, case, oracle.T_TAYLOR, table_n, level)
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32).upload()
+    o = psr.Options(precision=psr.PSR_FP64, table_n=table_n, interp=interp)
+    acc = lv.forces(o).cpu().numpy()
+    lv.check()
+    assert acc.dtype == np.float64
+    assert rel_rms(acc, ref) < 1e-12
+    exact, _, _ = oracle_acc(b, case)
+    assert rel_rms(acc, exact) < (1e-11 if level == 4 else 1e-7)
+    lv.forces(psr.Options(precision=psr.PSR_FP64, table_n=table_n, interp=interp,
+                          count_pairs=True))
+    assert lv.pair_count() == int(pairs.sum())
+
+
+def test_fp64_taylor_table_argument_rules():
+    """Forward-only: the adjoint and the allocation-free entry point refuse
+    it; switching between table kinds rebuilds the table each time."""
+    b = CASES["clustered"]()
+    lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32).upload()
+    o64 = psr.Options(precision=psr.PSR_FP64, interp=psr.PSR_TAYLOR4)
+    cot = torch.zeros((b.n, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(psr.PsrError) as e:
+        lv.adjoint(cot, o64)
+    assert e.value.code == capi.PSR_E_ARG
+    out = torch.empty((b.n, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_p2p_forces_noalloc(lv._h, o64.c(), out.data_ptr(), 0)
+    assert e.value.code == capi.PSR_E_ARG
+    a1 = lv.forces(o64).cpu().numpy()
+    lv.forces(psr.Options(precision=psr.PSR_FP32_TABLE, interp=psr.PSR_TAYLOR4))
+    a2 = lv.forces(o64).cpu().numpy()
+    np.testing.assert_array_equal(a1, a2)
