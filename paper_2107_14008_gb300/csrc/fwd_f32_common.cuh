@@ -508,20 +508,38 @@ __device__ __forceinline__ bool prefer_two_per_lane(int n)
     return e2 > 2 * e1 + (2 * e1) / 16;  // > 6 % better
 }
 
-// Targets per lane for the scalar kernel: 3 where it fills clearly more lane
-// slots than 1 or 2 (leaves of 17-18 and 21-24 particles: 24 = 8 lanes x 3
-// targets x 4 streams), else the choice above.  Three target slots need
-// 3 x 768 B of the warp's staging buffer for the final reduction, so only
-// with tiles of at least 128 particles.
+// Targets per lane for the scalar kernel, by cost per useful pair.  One
+// iteration of a stream evaluates one staged source against the lane's R
+// targets, kPairInstr instructions per target plus kSourceInstr for the
+// source itself (its shared-memory load and the loop), and the warp's
+// S_R = floor(32 / ceil(n_I / R)) streams serve n_I S_R pairs per iteration:
+// the cost per pair is (kPairInstr R + kSourceInstr) / S_R, the cheapest R
+// wins, ties going to the smaller.  The per-source term is set to 0, the
+// measured best: with 3, 6 or 10 the rule moves leaves of 25-32 particles to
+// R = 2 or 3 at equal lane fill, and whole launches ran 2-5 % slower.  So a
+// larger R is taken only where it fills strictly more lanes: R = 3 for
+// leaves of 3, 6, 9, 11-12, 17-18, 21-24 (24 = 8 lanes x 3 targets x 4
+// streams) and 33-48 particles (11-16 lanes x 2 streams, against 17-24 lanes
+// x 1 for R = 2; 6 % faster on leaves of up to 64); R = 2 for 19-20 and
+// 49-64.  R = 1 needs n_I <= 32; R = 3 needs tiles of at least 128
+// particles (its final reduction takes 3 x 768 B of the warp's staging
+// buffer).
+constexpr int kPairInstr = 20, kSourceInstr = 0;
 __device__ __forceinline__ int targets_per_lane(int n, int cap)
 {
-    const int two = prefer_two_per_lane(n) ? 2 : 1;
-    if (n > 32 || cap < 128) return two;
-    const int t3 = (n + 2) / 3;
-    const int e3 = n * (32 / t3);                               // x 1/96
-    const int eb = two == 2 ? n * (32 / ((n + 1) >> 1)) : n * (32 / n);  // x 1/64 or 1/32
-    const int eb96 = two == 2 ? eb * 3 / 2 : eb * 3;            // x 1/96
-    return e3 > eb96 + eb96 / 16 ? 3 : two;                     // > 6 % better
+    int best = 0, bnum = 0, bS = 1;
+#pragma unroll
+    for (int R = 1; R <= 3; ++R) {
+        const int T = (n + R - 1) / R;
+        if (T > 32 || (R == 3 && cap < 128)) continue;
+        const int S = 32 / T, num = kPairInstr * R + kSourceInstr;
+        if (best == 0 || num * bS < bnum * S) {
+            best = R;
+            bnum = num;
+            bS = S;
+        }
+    }
+    return best;
 }
 
 // Shared memory: the table, then one staging buffer of stage_cap particles
@@ -601,8 +619,8 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 template <int TM, int ACC, bool COUNT, bool PK>
 static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    // The scalar kernel always carries the two-targets-per-lane path: leaves of
-    // 11-12 and 17-20 particles fill more lanes with it (prefer_two_per_lane).
+    // The scalar kernel always carries the paths of two and three targets per
+    // lane (targets_per_lane picks one per leaf).
     auto k = (!PK || a.max_leaf > 32) ? p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>
                                       : p2p_fwd_f32_kernel<TM, ACC, COUNT, false, PK>;
     if (smem > 48 * 1024) {

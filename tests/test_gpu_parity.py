@@ -118,6 +118,29 @@ def test_wide_leaves_two_targets_per_lane(case, kernel, interp):
     assert rel_rms(acc, ref) < 2e-5
 
 
+@pytest.mark.parametrize("tile", [64, 128, 256])
+@pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
+def test_each_targets_per_lane_class(tile, accum):
+    """The scalar kernel puts 1, 2 or 3 targets on a lane by leaf size (3 for
+    leaves of 3, 6, 9, 11-12, 17-18, 21-24 and 33-48 particles with tiles of
+    128 or more, 2 for 19-20 and 49-64; with 64-particle tiles only 1 or 2).
+    Each group of leaf sizes is checked on its own targets, so one wrong path
+    cannot hide in the mean over all particles."""
+    b = CASES["clustered"]()
+    ref, _, _ = oracle_acc(b, "clustered")
+    acc, lv = gpu_forces(b, psr.Options(accum=accum, source_tile=tile), 64)
+    leaf, perm = lv.host_arrays()["leaf"], lv.perm
+    size = np.zeros(b.n, np.int64)
+    for first, cnt in leaf[:, :2]:
+        size[perm[first:first + cnt]] = cnt
+    three = [3, 6, 9, 11, 12, 17, 18, 21, 22, 23, 24] + list(range(33, 49))
+    classes = {"three": np.isin(size, three), "two": np.isin(size, [19, 20] + list(range(49, 65)))}
+    classes["one"] = ~(classes["three"] | classes["two"])
+    for name, sel in classes.items():
+        assert sel.sum() > 100, name
+        assert rel_rms(acc[sel], ref[sel]) < 2e-5, name
+
+
 @pytest.mark.parametrize("case", ["uniform", "clustered"])
 @pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
                                          (psr.PSR_CUBIC, oracle.T_CUBIC)])
