@@ -143,6 +143,11 @@ typedef struct {
                                 psr_device_build_split handle, else 0; n_pairs
                                 then counts the near (P2P) entries only        */
     double theta;            /* acceptance parameter of that split, else 0    */
+    int64_t rows_walked_twice; /* device builds: target leaves whose pair row
+                                the count walk could not keep in the pair
+                                cache, walked again by psr_device_build_finish
+                                (every row for a split or when the cache's
+                                per-row slot is below 16 runs); else 0      */
 } psr_info;
 
 typedef struct psr_leaves psr_leaves; /* opaque, host-owned */
@@ -368,7 +373,9 @@ int psr_leaves_regions(const psr_leaves* h, psr_regions* out);
  * size the workspace from the counts:
  *
  * psr_device_build_scratch_bytes - host: scratch bytes psr_device_build
- * needs for n particles (about 360 per particle).  Errors: PSR_E_ARG
+ * needs for n particles (about 430 per particle, 64 of them a cache of the
+ * pair rows the counting walk finds, which psr_device_build_finish then
+ * copies instead of walking the tree again).  Errors: PSR_E_ARG
  * (n < 1 or n > 2^28, NULL).
  *
  * psr_device_build - enqueue key, radix sort, leaf, radix tree and pair

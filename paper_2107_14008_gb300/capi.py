@@ -52,7 +52,8 @@ class psr_info(ctypes.Structure):
                 ("evaluated_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("max_leaf", ctypes.c_int), ("max_row", ctypes.c_int),
                 ("build_seconds", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
-                ("n_far", ctypes.c_int64), ("theta", ctypes.c_double)]
+                ("n_far", ctypes.c_int64), ("theta", ctypes.c_double),
+                ("rows_walked_twice", ctypes.c_int64)]
 
 
 class psr_host_arrays(ctypes.Structure):

@@ -275,6 +275,7 @@ int psr_leaves_info(const psr_leaves* hh, psr_info* info)
     info->perm = h->device_built ? nullptr : h->perm.data();
     info->n_far = h->n_far;
     info->theta = h->theta;
+    info->rows_walked_twice = h->device_built ? h->db_uncached : 0;
     return PSR_OK;
 }
 

@@ -17,8 +17,11 @@
 //                contains its leaves' boxes, so the kept set is exactly the set of
 //                leaves that pass the leaf test, which the host's octree keeps too;
 //                the left-first order visits them in leaf order like the host's
-//                Morton-ordered octree walk.  Counted in one pass, written in a
-//                second after a prefix sum of the counts.  The walk prunes with
+//                Morton-ordered octree walk.  Counted in one pass, which also
+//                stores each row in a pair cache of 16 words per particle; after
+//                a prefix sum of the counts the cached rows are copied into
+//                place and only the rows the cache could not hold are walked a
+//                second time (the multipole split walks twice).  The walk prunes with
 //                FP32 bounds (directed rounding) and falls back to the host's FP64
 //                leaf test only where the bounds cannot decide (gap^2 within about
 //                1e-5 of the cutoff): FP64 throughput on this part is 1/64 of FP32.
@@ -62,15 +65,27 @@ enum : int {
     kCntMaxRow = 4,
     kCntError = 5,  // bit 0 non-finite input, bit 1 stack overflow, bit 2 malformed tree
     kCntFar = 6,    // well-separated (M2L) entries of the multipole split
+    kCntUncached = 7,  // rows the pair cache could not hold (re-walked by the write pass)
     kCntWords = 8,
 };
+
+// The pair cache: the count walk also records each row as runs of
+// consecutive leaves of one image (the first leaf with its image code, and the
+// run length: 8 bytes, one run for about ten entries on clustered sets), in a
+// slot of equal size per row, so that the write step expands the runs instead
+// of walking the tree again.  A row with more runs than its slot holds is
+// walked again instead; with slots below kMinRuns runs the cache is not used.
+constexpr int kCacheWordsPerParticle = 16;
+constexpr int kMinRuns = 16;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Scratch regions (byte offsets); leaf arrays are sized for n leaves (max_leaf 1).
 struct Scratch {
     size_t wpos, key0, key1, val0, val1, flag, lid, lfirst, llevel, lkey, lbox, lrec, lcnt,
-        lfar, lout, lcost, tnode, tspan, tparl, tpari, tbox, nodef, tflag, hist, tiles, total, cnt, bytes;
+        lfar, lout, lcost, tnode, tspan, tparl, tpari, tbox, nodef, tflag, hist, tiles, total, cnt,
+        lruns, cache, bytes;
+    int64_t ncache;  // pair cache capacity in runs
 };
 
 Scratch scratch_layout(int64_t n)
@@ -109,6 +124,9 @@ Scratch scratch_layout(int64_t n)
     s.tiles = o;  o = a256(o + 8 * ntiles);
     s.total = o;  o = a256(o + 8);
     s.cnt = o;    o = a256(o + 8 * kCntWords);
+    s.lruns = o;  o = a256(o + 4 * N);   // runs cached per row (-1: not cached)
+    s.ncache = (int64_t)(kCacheWordsPerParticle / 2 * N);
+    s.cache = o;  o = a256(o + 8 * (size_t)s.ncache);  // uint2 (first leaf << 5 | code, length)
     s.bytes = o;
     return s;
 }
@@ -794,8 +812,11 @@ __device__ __forceinline__ bool far_pair(const float* alo, const float* ahi, flo
     return d2 > 0.f && m2 < rc2far && __fmul_rn(theta2, d2) >= r2 && __fmul_rn(r2, d2) <= gt2;
 }
 
-// One thread per target leaf.  WRITE = false counts the row and its work;
-// WRITE = true writes the row at rowptr.  Nodes are pruned when the FP32
+// One thread per target leaf.  WRITE = false counts the row and its work
+// and, given a pair cache of kslot runs per row, records the row's runs there
+// in walk order (lruns[I]: their number, or -1 when the slot is too small);
+// WRITE = true writes the row at rowptr, skipping the rows a given lruns
+// marks as cached (k_pairs_expand writes those).  Nodes are pruned when the FP32
 // lower bound of their gap^2 reaches thi (then the host's FP64 test fails
 // for every leaf below); a leaf is kept when the FP32 upper bound is below
 // tlo (then the host's FP64 test passes); only the leaves in between take
@@ -809,10 +830,12 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
     const double* __restrict__ lbox, const float4* __restrict__ lrec,
     const float4* __restrict__ nodef, const double* __restrict__ rootbox,
     int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, const int64_t* __restrict__ rowptr,
-    uint32_t* __restrict__ pairs, long long* __restrict__ cnt, unsigned* __restrict__ err)
+    uint32_t* __restrict__ pairs, long long* __restrict__ cnt, unsigned* __restrict__ err,
+    int32_t* __restrict__ lruns, uint2* __restrict__ cache, int kslot)
 {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= nl) return;
+    if (WRITE && lruns && lruns[I] >= 0) return;
     double A[6];
     float aolo[3], aohi[3], ailo[3], aihi[3], rlo[3], rhi[3];
     for (int a = 0; a < 3; ++a) {
@@ -831,6 +854,13 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
     int64_t w = WRITE ? rowptr[I] : 0;
     const int64_t wend = WRITE ? rowptr[I + 1] : 0;
     bool bad = false;
+    // pair cache state: the open run (first entry word, length) and the runs
+    // stored so far in this row's slot
+    const bool caching = !WRITE && cache != nullptr;
+    bool cok = caching;
+    uint2* const slot = caching ? cache + I * (int64_t)kslot : nullptr;
+    uint32_t run0 = 0, runn = 0;
+    int nrun = 0;
     // keeps leaves [f, l] of this image
     auto take = [&](int f, int l, int code) {
         c += l - f + 1;
@@ -842,6 +872,21 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
                 return;
             }
             for (int J = f; J <= l; ++J) pairs[w++] = ((uint32_t)J << 5) | (uint32_t)code;
+        } else if (cok) {
+            const uint32_t e0 = ((uint32_t)f << 5) | (uint32_t)code;
+            if (runn > 0 && e0 == run0 + (runn << 5)) {  // continues the open run
+                runn += (uint32_t)(l - f + 1);
+            } else {
+                if (runn > 0) {
+                    if (nrun == kslot) {
+                        cok = false;
+                        return;
+                    }
+                    slot[nrun++] = make_uint2(run0, runn);
+                }
+                run0 = e0;
+                runn = (uint32_t)(l - f + 1);
+            }
         }
     };
     for (int code = 0; code < kShiftCodes && !bad; ++code) {
@@ -920,10 +965,47 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
         const int64_t nI = lfirst[I + 1] - lfirst[I];
         lcnt[I] = c;
         lcost[I] = src * nI;
+        if (caching) {
+            if (cok && runn > 0) {
+                if (nrun == kslot)
+                    cok = false;
+                else
+                    slot[nrun++] = make_uint2(run0, runn);
+            }
+            lruns[I] = cok ? nrun : -1;
+            if (!cok) atomicAdd((unsigned long long*)(cnt + kCntUncached), 1ULL);
+        }
         atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
         atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
         atomicMax(cnt + kCntMaxCost, (long long)(src * nI));
         atomicMax(cnt + kCntMaxRow, (long long)c);
+    }
+}
+
+// Writes the cached rows at rowptr: one warp per row expands its runs, 32
+// entries per step.  A run list that does not add up to the row's length
+// (a corrupt cache) sets error bit 4.
+__global__ void __launch_bounds__(256) k_pairs_expand(int64_t nl, const int32_t* __restrict__ lruns,
+                                                      const uint2* __restrict__ cache, int kslot,
+                                                      const int64_t* __restrict__ rowptr,
+                                                      uint32_t* __restrict__ pairs,
+                                                      unsigned* __restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t I = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); I < nl; I += nw) {
+        const int nrun = lruns[I];
+        if (nrun <= 0) continue;  // empty, or walked by the write pass
+        const uint2* slot = cache + I * (int64_t)kslot;
+        int64_t dst = rowptr[I];
+        const int64_t end = rowptr[I + 1];
+        for (int r = 0; r < nrun; ++r) {
+            const uint2 run = slot[r];
+            if (dst + run.y > end) break;
+            for (uint32_t k = lane; k < run.y; k += 32) pairs[dst + k] = run.x + (k << 5);
+            dst += run.y;
+        }
+        if (dst != end && lane == 0) atomicOr(err, 4u);
     }
 }
 
@@ -936,6 +1018,9 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
 // and counts or writes the near and far entries of each owning row in walk
 // order.  Every lane runs the same number of flushes (lanes past the last
 // leaf have ended from the start), so the warp-wide steps see all 32 lanes.
+// With a pair cache the count pass also records each row's queued ranges as
+// runs (as k_pairs does), and the write pass replays a recorded row's runs
+// into the queue instead of walking it again (lruns[I] >= 0).
 constexpr int kSplitQ = 8;  // queued ranges per lane (a walk step queues at most 2)
 
 template <bool WRITE>
@@ -946,7 +1031,8 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
     int64_t* __restrict__ lcnt, int64_t* __restrict__ lcost, int64_t* __restrict__ lfar,
     const int64_t* __restrict__ rowptr, uint32_t* __restrict__ pairs,
     const int64_t* __restrict__ frowptr, uint32_t* __restrict__ fpairs,
-    long long* __restrict__ cnt, unsigned* __restrict__ err)
+    long long* __restrict__ cnt, unsigned* __restrict__ err, int32_t* __restrict__ lruns,
+    uint2* __restrict__ cache, int kslot)
 {
     constexpr int kQ = kSplitQ, kSlots = 32 * kSplitQ, kWarps = 4;
     __shared__ int4 sq[kWarps][kSlots];            // (first, last, image, owning lane)
@@ -995,10 +1081,46 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
     float sd[3] = {0.f, 0.f, 0.f}, su[3] = {0.f, 0.f, 0.f};
     double sh[3] = {0.0, 0.0, 0.0};
     int4* myq = &sq[wp][lane * kQ];
+    // pair cache: the count pass records runs (open run run0/runn), the write
+    // pass replays a recorded row (nrun runs, the next one at ri)
+    bool cok = !WRITE && live && cache != nullptr;
+    const bool replay = WRITE && live && lruns != nullptr && lruns[I] >= 0;
+    uint2* const slot = (cok || replay) ? cache + I * (int64_t)kslot : nullptr;
+    uint32_t run0 = 0, runn = 0;
+    int nrun = replay ? lruns[I] : 0, ri = 0;
+    int nq = 0;
+    auto push = [&](int f, int l, int c) {
+        myq[nq++] = make_int4(f, l, c, lane);
+        if (!cok) return;
+        const uint32_t e0 = ((uint32_t)f << 5) | (uint32_t)c;
+        if (runn > 0 && e0 == run0 + (runn << 5)) {
+            runn += (uint32_t)(l - f + 1);
+        } else {
+            if (runn > 0) {
+                if (nrun == kslot) {
+                    cok = false;
+                    return;
+                }
+                slot[nrun++] = make_uint2(run0, runn);
+            }
+            run0 = e0;
+            runn = (uint32_t)(l - f + 1);
+        }
+    };
     for (;;) {
-        // ---- walk until the queue may not take another step's ranges
-        int nq = 0;
+        // ---- walk (or replay) until the queue may not take another step's ranges
+        nq = 0;
         while (!done && nq <= kQ - 2) {
+            if (replay) {
+                if (ri == nrun) {
+                    done = true;
+                    break;
+                }
+                const uint2 run = slot[ri++];
+                const int f = (int)(run.x >> 5);
+                myq[nq++] = make_int4(f, f + (int)run.y - 1, (int)(run.x & 31u), lane);
+                continue;
+            }
             if (!in_tree) {
                 if (++code >= kShiftCodes) {
                     done = true;
@@ -1013,7 +1135,7 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
                 }
                 if (gap2_lower(aolo, aohi, rlo, rhi, sd, su) >= bx.thi) continue;
                 if (maxgap2_upper(ailo, aihi, rlo, rhi, sd, su) < bx.tlo) {
-                    myq[nq++] = make_int4(0, (int)nl - 1, code, lane);
+                    push(0, (int)nl - 1, code);
                     continue;
                 }
                 in_tree = true;
@@ -1028,14 +1150,14 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
             }
             int2 next = make_int2(0, -2);  // y == -2: take the next stacked entry
             if (cur.y >= 0) {  // a whole leaf range deferred behind a left subtree
-                myq[nq++] = make_int4(cur.x, cur.y, code, lane);
+                push(cur.x, cur.y, code);
             } else if (cur.x < 0) {  // a leaf that passed the lower-bound test
                 const int J = cur.x & 0x7fffffff;
                 const float4 r0 = lrec[2 * (int64_t)J], r1 = lrec[2 * (int64_t)J + 1];
                 const float bi_lo[3] = {r0.x, r0.y, r0.z}, bi_hi[3] = {r1.x, r1.y, r1.z};
                 if (gap2_upper(ailo, aihi, bi_lo, bi_hi, sd, su) < bx.tlo ||
                     gap2_d(A, lbox + 6 * (int64_t)J, sh) < bx.rc2m)
-                    myq[nq++] = make_int4(J, J, code, lane);
+                    push(J, J, code);
             } else {
                 const float4* qn = nodef + 4 * (int64_t)cur.x;
                 const float4 q0 = qn[0], q1 = qn[1], q2 = qn[2], q3 = qn[3];
@@ -1048,7 +1170,7 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
                 const bool pr = gap2_lower(aolo, aohi, blo, bhi, sd, su) < bx.thi;
                 const bool fl = pl && maxgap2_upper(ailo, aihi, llo, lhi, sd, su) < bx.tlo;
                 const bool fr = pr && maxgap2_upper(ailo, aihi, blo, bhi, sd, su) < bx.tlo;
-                if (fl) myq[nq++] = make_int4(lo, gamma, code, lane);
+                if (fl) push(lo, gamma, code);
                 if (pl && !fl) {  // the left child needs a visit; the right one waits
                     if (pr) {
                         if (sp >= kStackDepth) {
@@ -1060,7 +1182,7 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
                     }
                     next = make_int2(lc, -1);
                 } else if (fr) {
-                    myq[nq++] = make_int4(gamma + 1, hi, code, lane);
+                    push(gamma + 1, hi, code);
                 } else if (pr) {
                     next = make_int2(rc, -1);
                 }
@@ -1161,6 +1283,16 @@ __global__ void __launch_bounds__(128, 4) k_pairs_split(
         lcnt[I] = c;
         lfar[I] = cf;
         lcost[I] = src * nI;
+        if (cache) {
+            if (cok && runn > 0) {
+                if (nrun == kslot)
+                    cok = false;
+                else
+                    slot[nrun++] = make_uint2(run0, runn);
+            }
+            lruns[I] = cok ? nrun : -1;
+            if (!cok) atomicAdd((unsigned long long*)(cnt + kCntUncached), 1ULL);
+        }
         atomicAdd((unsigned long long*)(cnt + kCntPairs), (unsigned long long)c);
         atomicAdd((unsigned long long*)(cnt + kCntFar), (unsigned long long)cf);
         atomicAdd((unsigned long long*)(cnt + kCntEvaluated), (unsigned long long)(src * nI));
@@ -1425,15 +1557,21 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
         k_tree_pack<<<nblk(nl - 1, 256), 256, 0, st>>>(nl, tnode, tspan, lbox, tbox, nodef);
     }
     const double* rootbox = nl >= 2 ? tbox : lbox;
+    // runs per row in the pair cache (none below kMinRuns: rows walked twice)
+    const int64_t ks = S.ncache / nl;
+    const int kslot = ks >= kMinRuns ? (int)(ks < (1 << 20) ? ks : (1 << 20)) : 0;
+    int32_t* const lruns = kslot ? (int32_t*)(s + S.lruns) : nullptr;
+    uint2* const pcache = kslot ? (uint2*)(s + S.cache) : nullptr;
     if (theta > 0.0)
         k_pairs_split<false><<<nblk(nl, 128), 128, 0, st>>>(
             nl, bx, lfirst, lbox, lrec, (const float4*)(s + S.lout), nodef, rootbox, lcnt, lcost,
             (int64_t*)(s + S.lfar), nullptr, nullptr, nullptr, nullptr, cnt,
-            (unsigned*)(cnt + kCntError));
-    else
-        k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(nl, n, bx, lfirst, lbox, lrec, nodef,
-                                                      rootbox, lcnt, lcost, nullptr, nullptr, cnt,
-                                                      (unsigned*)(cnt + kCntError));
+            (unsigned*)(cnt + kCntError), lruns, pcache, kslot);
+    else {
+        k_pairs<false><<<nblk(nl, 128), 128, 0, st>>>(
+            nl, n, bx, lfirst, lbox, lrec, nodef, rootbox, lcnt, lcost, nullptr, nullptr, cnt,
+            (unsigned*)(cnt + kCntError), lruns, pcache, kslot);
+    }
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair count kernel");
     if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
     if (c[kCntError] & 2) return dfail(PSR_E_DEVICE, "tree traversal stack overflow");
@@ -1468,6 +1606,8 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     }
     h->db_scratch = s;
     h->db_maxcost = c[kCntMaxCost];
+    h->db_kslot = kslot;
+    h->db_uncached = kslot ? c[kCntUncached] : nl;
     h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = reinterpret_cast<psr_leaves*>(h);
     return PSR_OK;
@@ -1548,16 +1688,28 @@ int psr_device_build_finish(psr_leaves* hh, void* d_ws, size_t bytes, void* stre
         bxw.gt2 = (h->flags & PSR_BUILD_SPLIT_GAUSSIAN)
                       ? (float)(h->theta * h->theta * 4.0 * std::pow(h->boxes[0].r_s, 4))
                       : INFINITY;
+        // rows the count pass recorded are replayed; the rest are walked again
         k_pairs_split<true><<<nblk(nl, 128), 128, 0, st>>>(
             nl, bxw, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.lout),
             (const float4*)(s + S.nodef), rootbox, nullptr, nullptr, nullptr, rowptr,
             (uint32_t*)(w + L.pairs), frow, (uint32_t*)(w + L.fpairs), nullptr,
-            (unsigned*)(w + L.ctrl) + kCtrlError);
+            (unsigned*)(w + L.ctrl) + kCtrlError,
+            h->db_kslot ? (int32_t*)(s + S.lruns) : nullptr,
+            h->db_kslot ? (uint2*)(s + S.cache) : nullptr, h->db_kslot);
     } else {
-        k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
-            nl, n, bx, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.nodef),
-            rootbox, nullptr, nullptr, rowptr, (uint32_t*)(w + L.pairs), nullptr,
-            (unsigned*)(w + L.ctrl) + kCtrlError);
+        // rows the count walk cached are expanded; the rest are walked again
+        int32_t* lruns = h->db_kslot ? (int32_t*)(s + S.lruns) : nullptr;
+        if (lruns) {
+            k_pairs_expand<<<nblk(nl, 8), 256, 0, st>>>(nl, lruns, (const uint2*)(s + S.cache),
+                                                       h->db_kslot, rowptr, (uint32_t*)(w + L.pairs),
+                                                       (unsigned*)(w + L.ctrl) + kCtrlError);
+            if ((e = (int)cudaGetLastError())) return dcuda(e, "pair expand kernel");
+        }
+        if (h->db_uncached > 0)
+            k_pairs<true><<<nblk(nl, 128), 128, 0, st>>>(
+                nl, n, bx, lfirst, lbox, (const float4*)(s + S.lrec), (const float4*)(s + S.nodef),
+                rootbox, nullptr, nullptr, rowptr, (uint32_t*)(w + L.pairs), nullptr,
+                (unsigned*)(w + L.ctrl) + kCtrlError, lruns, nullptr, 0);
     }
     if ((e = (int)cudaGetLastError())) return dcuda(e, "pair write kernel");
     // schedule: the particle sort buffers are free again (values in int32

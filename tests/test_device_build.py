@@ -122,11 +122,44 @@ def _compare(host, gpu):
     assert np.array_equal(gpu.perm, host.perm)
 
 
+def _runs_per_row(A):
+    """Maximal runs of consecutive leaves of one image code in each row."""
+    rp, p = A["rowptr"], A["pairs"].astype(np.int64)
+    if p.size == 0:
+        return np.zeros(rp.size - 1, np.int64)
+    brk = np.ones(p.size, bool)
+    brk[1:] = p[1:] != p[:-1] + 32  # next leaf, same code
+    starts = rp[:-1]
+    brk[starts[starts < p.size]] = True
+    cs = np.concatenate([[0], np.cumsum(brk)])
+    return cs[rp[1:]] - cs[rp[:-1]]
+
+
+def _check_pair_cache(b, host, gpu):
+    """The count walk keeps a row as its runs in a slot of floor(8 n / n_leaves)
+    runs (the cache is unused below 16); rows with more runs are walked a second
+    time.  The walk's runs are the maximal runs of the final row, so the host's
+    list fixes how many rows that is."""
+    nl = host.info.n_leaves
+    kslot = min(8 * max(b.n, 1) // nl, 1 << 20)
+    want = nl if kslot < 16 else int(np.sum(_runs_per_row(host.host_arrays()) > kslot))
+    assert gpu.info.rows_walked_twice == want
+    return want
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_device_build_equals_host_build(case):
+    """Bit for bit, whether the pair rows come from the count walk's cache
+    (clustered, nfw64, ...), from a second walk (clustered_leaf1 and
+    lattice_cutoff1: slots below 16 runs) or from both (clustered_leaf8)."""
     b = CASES[case]()
     host, gpu = _build_both(b)
     _compare(host, gpu)
+    twice = _check_pair_cache(b, host, gpu)
+    if case == "clustered_leaf8":
+        assert 0 < twice < host.info.n_leaves
+    if case in ("clustered", "nfw64", "uniform20"):
+        assert twice == 0
 
 
 @pytest.mark.parametrize("fp64,masses", [(False, True), (True, False)])
@@ -224,5 +257,6 @@ def test_device_build_unpacked_equals_host_unpacked(case):
     mass_d = torch.tensor(b.mass, dtype=torch.float64, device=dev)
     gpu = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, b.max_leaf, pack=False)
     _compare(host, gpu)
+    _check_pair_cache(b, host, gpu)
     packed = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, b.max_leaf)
     assert packed.info.n_leaves <= host.info.n_leaves

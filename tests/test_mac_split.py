@@ -114,6 +114,8 @@ def test_split_partitions_the_pair_list_by_the_acceptance_test(case, theta, gaus
     fi, si = full.info, split.info
     assert si.theta == theta and fi.n_far == 0
     assert si.n_leaves == fi.n_leaves
+    # both count walks record the same kept ranges in the pair cache
+    assert si.rows_walked_twice == fi.rows_walked_twice
     assert si.n_pairs + si.n_far == fi.n_pairs
     DF, DS, F = full.device_arrays(), split.device_arrays(), split.far_arrays()
     for k in ("leaf", "lcen", "perm"):
