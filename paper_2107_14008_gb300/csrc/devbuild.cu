@@ -1388,7 +1388,13 @@ int dcuda(int e, const char* what)
 }
 
 // Bounded host wait for the stream, then a copy of `bytes` to the host.
-int read_back(void* dst, const void* src, size_t bytes, cudaStream_t st, int timeout_ms)
+// Waits (at most timeout_ms) for the work queued on st, then copies one or
+// two small device blocks to the host.  The wait polls without sleeping for
+// its first 2 ms (the build's steps between waits take about a millisecond,
+// and a sleeping poll wakes up to tens of microseconds late), then every 20
+// microseconds.
+int read_back(void* dst, const void* src, size_t bytes, cudaStream_t st, int timeout_ms,
+              void* dst2 = nullptr, const void* src2 = nullptr, size_t bytes2 = 0)
 {
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -1397,9 +1403,10 @@ int read_back(void* dst, const void* src, size_t bytes, cudaStream_t st, int tim
         if (e != cudaErrorNotReady) return dcuda(e, "cudaStreamQuery");
         double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (ms > timeout_ms) return dfail(PSR_E_TIMEOUT, "device build did not finish within the timeout");
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        if (ms > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && dst2) e = cudaMemcpyAsync(dst2, src2, bytes2, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? PSR_OK : dcuda(e, "cudaMemcpyAsync (device build counters)");
 }
@@ -1520,8 +1527,7 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
     if ((e = (int)cudaGetLastError())) return dcuda(e, "leaf fill kernel");
     long long c[kCntWords];
     int64_t nl = 0;
-    if ((e = read_back(&nl, total, 8, st, timeout_ms))) return e;
-    if ((e = read_back(c, cnt, sizeof c, st, timeout_ms))) return e;
+    if ((e = read_back(&nl, total, 8, st, timeout_ms, c, cnt, sizeof c))) return e;
     if (c[kCntError] & 1) return dfail(PSR_E_ARG, "non-finite position or mass");
     if (nl < 1 || nl > n || nl >= (1 << 27)) return dfail(PSR_E_ARG, "leaf count out of range");
     if (!(flags & PSR_BUILD_UNPACKED)) {
