@@ -982,9 +982,12 @@ __global__ void __launch_bounds__(128, 8) k_pairs(
     }
 }
 
-// Writes the cached rows at rowptr: one warp per row expands its runs, 32
-// entries per step.  A run list that does not add up to the row's length
-// (a corrupt cache) sets error bit 4.
+// Writes the cached rows at rowptr.  One warp per row: lane k loads run k of
+// a group of 32 (one coalesced load), a warp scan of the run lengths gives
+// each run's first entry, and the group's entries are written 32 at a time,
+// entry e finding its run by a binary search over the lanes (shuffles).  A
+// run list that does not add up to the row's length (a corrupt cache) sets
+// error bit 4.
 __global__ void __launch_bounds__(256) k_pairs_expand(int64_t nl, const int32_t* __restrict__ lruns,
                                                       const uint2* __restrict__ cache, int kslot,
                                                       const int64_t* __restrict__ rowptr,
@@ -997,15 +1000,38 @@ __global__ void __launch_bounds__(256) k_pairs_expand(int64_t nl, const int32_t*
         const int nrun = lruns[I];
         if (nrun <= 0) continue;  // empty, or walked by the write pass
         const uint2* slot = cache + I * (int64_t)kslot;
-        int64_t dst = rowptr[I];
-        const int64_t end = rowptr[I + 1];
-        for (int r = 0; r < nrun; ++r) {
-            const uint2 run = slot[r];
-            if (dst + run.y > end) break;
-            for (uint32_t k = lane; k < run.y; k += 32) pairs[dst + k] = run.x + (k << 5);
-            dst += run.y;
+        const int64_t row0 = rowptr[I], len = rowptr[I + 1] - row0;
+        int64_t done = 0;  // entries of the earlier groups
+        bool bad = false;
+        for (int r0 = 0; r0 < nrun; r0 += 32) {
+            const int nv = nrun - r0 < 32 ? nrun - r0 : 32;
+            const uint2 run = lane < nv ? slot[r0 + lane] : make_uint2(0u, 0u);
+            int64_t inc = run.y;  // inclusive scan of the run lengths
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t v = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const int64_t tot = __shfl_sync(kFull, inc, 31);
+            const int64_t exc = inc - run.y;
+            if (done + tot > len) {
+                bad = true;
+                break;
+            }
+            for (int64_t e0 = 0; e0 < tot; e0 += 32) {
+                const int64_t e = e0 + lane;
+                int lo = 0;  // the last run whose first entry is <= e
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int cand = lo + step;
+                    const int64_t v = __shfl_sync(kFull, exc, cand & 31);
+                    if (cand < nv && v <= e) lo = cand;
+                }
+                const uint32_t x = __shfl_sync(kFull, run.x, lo);
+                const int64_t first = __shfl_sync(kFull, exc, lo);
+                if (e < tot) pairs[row0 + done + e] = x + ((uint32_t)(e - first) << 5);
+            }
+            done += tot;
         }
-        if (dst != end && lane == 0) atomicOr(err, 4u);
+        if ((bad || done != len) && lane == 0) atomicOr(err, 4u);
     }
 }
 
