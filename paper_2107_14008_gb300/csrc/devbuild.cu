@@ -411,9 +411,11 @@ __global__ void k_keys(const double* __restrict__ pos, const double* __restrict_
             bad = true;
             v = 0.0;
         }
-        v = fmod(v, bx.L);
-        if (v < 0) v += bx.L;
-        if (!(v < bx.L)) v = 0.0;
+        if (!(v >= 0.0 && v < bx.L)) {  // fmod is exact, so values inside [0, L) keep their bits
+            v = fmod(v, bx.L);
+            if (v < 0) v += bx.L;
+            if (!(v < bx.L)) v = 0.0;
+        }
         wpos[4 * i + a] = v;
         double qq = floor(__dmul_rn(v, bx.scale));
         if (qq < 0) qq = 0;
