@@ -338,6 +338,7 @@ def test_regions_of_a_host_built_handle():
     lv = psr.Leaves.build(rng.random((3000, 3)) * 20.0, None, 20.0, 1.5, 6.75)
     r = capi.psr_leaves_regions(lv._h)
     inf = lv.info
+    assert inf.rows_walked_twice == 0 and inf.n_far == 0  # device-build fields
     n, nl, npairs = 3000, inf.n_leaves, inf.n_pairs
     order = [("pf", 16 * n), ("pd", 32 * n), ("perm", 4 * n), ("leaf", 16 * nl),
              ("lcen", 16 * nl), ("rowptr", 8 * (nl + 1)), ("pairs", 4 * npairs),
