@@ -112,6 +112,7 @@ struct Leaves {
     char* db_scratch = nullptr; // device build between its two calls: the caller's scratch
     int64_t db_maxcost = 0;     //   and the largest per-leaf cost (schedule sort width)
     int db_kslot = 0;           //   runs per row in the pair cache (0: not used)
+    int db_interleave = 0;      //   whether the walks take rows interleaved over warps
     int64_t db_uncached = 0;    //   and the rows it could not hold
     // device state
     Layout lay{};
