@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--table-n", type=int, default=1024)
     p.add_argument("--interp", default="linear", choices=["linear", "cubic"])
     p.add_argument("--accum", default="fp64", choices=["fp64", "kahan"])
+    p.add_argument("--kernel", default="scalar", choices=["scalar", "packed"],
+                   help="FP32 forward inner loop: scalar streams (the default) or packed f32x2 "
+                        "pairs")
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--adjoint-steps", type=int, default=3)
@@ -569,7 +572,9 @@ def run_psr(args):
     info = lv.info
     opts = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=args.table_n,
                        interp=psr.PSR_LINEAR if args.interp == "linear" else psr.PSR_CUBIC,
-                       accum=psr.PSR_ACC_FP64 if args.accum == "fp64" else psr.PSR_ACC_KAHAN32)
+                       accum=psr.PSR_ACC_FP64 if args.accum == "fp64" else psr.PSR_ACC_KAHAN32,
+                       kernel=psr.PSR_KERNEL_PACKED if args.kernel == "packed"
+                       else psr.PSR_KERNEL_SCALAR)
     acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -873,7 +878,7 @@ def run_psr(args):
         "cpu_baseline": None if cb is None else {k: cb[k] for k in
                                                   ("value", "unit", "cores", "kind", "sample")},
         "gpu_launches": args.steps,
-        "tile_shape": {"kernel": "scalar streams", "warps_per_block": 8, "source_tile": 256},
+        "tile_shape": {"kernel": "packed f32x2 pairs" if args.kernel == "packed" else "scalar streams", "warps_per_block": 8, "source_tile": 256},
         "clocks": clocks,
         "device": props.name,
     }

@@ -255,11 +255,18 @@ int psr_p2p_adjoint(psr_leaves* h, const psr_opts* opts, const void* d_cot, void
  * The kernel's scratch (work counters, error word and interpolation table)
  * is a fixed 66,048-byte __device__ array in the library instead of the
  * workspace; each device that loads the library holds one copy until the
- * process exits.  Nothing is allocated by this call or by anything it calls.
+ * process exits.  The call never calls cudaMalloc, cudaFree or any other
+ * allocating routine.
  * Limits and behaviour:
  *  - PSR_FP32_TABLE accepts table_n <= 4096; larger tables return PSR_E_ARG.
- *  - The first call on each device looks up the array's device address with
- *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *  - Set-up: the first call on each device (with that device current) looks
+ *    up the array's device address with cudaGetSymbolAddress and caches it.
+ *    Under CUDA's default lazy module loading that look-up is what loads the
+ *    library's module holding the array onto the device, and the driver
+ *    allocates the array's storage at that moment.  A caller that cannot
+ *    allow even that makes one call on each device at start-up, before any
+ *    stream capture (or runs with CUDA_MODULE_LOADING=EAGER, which loads the
+ *    modules when the context is created); later calls allocate nothing.
  *  - Every call on a device shares the array: each call clears its counters
  *    and rebuilds the table it needs first, and two calls that overlap on
  *    the GPU (different streams, no ordering) race on it.

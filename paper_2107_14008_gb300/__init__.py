@@ -438,26 +438,34 @@ def _autograd_function():
     class P2PForce(torch.autograd.Function):
         """a = P2PForce.apply(pos, mass, L, r_s, r_c, G, opts, max_leaf).
 
-        Forward builds the leaf set on the host from `pos` and runs the
-        forward kernel; backward runs the adjoint kernel on the same pair set
-        (the set is frozen at the forward positions, so the gradient is that
-        of the piecewise function with the hard cutoff held fixed)."""
+        Forward builds the leaf set from `pos` and runs the forward kernel:
+        on the GPU (psr_device_build) when `pos` is a CUDA tensor, else on the
+        host (psr_build_leaves) and uploaded to the current CUDA device.
+        Backward runs the adjoint kernel on the same pair set (the set is
+        frozen at the forward positions, so the gradient is that of the
+        piecewise function with the hard cutoff held fixed)."""
 
         @staticmethod
         def forward(ctx, pos, mass, L, r_s, r_c, G=1.0, opts=None, max_leaf=32):
             opts = opts or Options()
-            lv = Leaves.build(pos, mass, L, r_s, r_c, G, max_leaf, fp64=opts.fp64)
-            lv.upload(pos.device)
+            if pos.is_cuda:
+                lv = Leaves.device_build(pos, mass, L, r_s, r_c, G, max_leaf, fp64=opts.fp64)
+            else:
+                lv = Leaves.build(pos, mass, L, r_s, r_c, G, max_leaf, fp64=opts.fp64)
+                lv.upload()
             acc = lv.forces(opts)
+            if acc.device != pos.device:
+                acc = acc.to(pos.device)
             ctx.leaves, ctx.opts = lv, opts
             ctx.pos_dtype, ctx.mass_dtype = pos.dtype, mass.dtype
             return acc.to(pos.dtype)
 
         @staticmethod
         def backward(ctx, grad_acc):
+            dev = grad_acc.device
             gp, gm = ctx.leaves.adjoint(grad_acc.contiguous(), ctx.opts)
-            return (gp.to(ctx.pos_dtype), gm.to(ctx.mass_dtype), None, None, None, None, None,
-                    None)
+            return (gp.to(device=dev, dtype=ctx.pos_dtype), gm.to(device=dev, dtype=ctx.mass_dtype),
+                    None, None, None, None, None, None)
 
     return P2PForce
 

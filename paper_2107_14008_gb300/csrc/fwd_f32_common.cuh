@@ -99,17 +99,77 @@ struct Acc3 {
     }
 };
 
+// The target leaf's particle box in the kernel's working frame, and the
+// cutoff in working units: a staged source particle whose distance from this
+// box is at least the cutoff is beyond the cutoff from every target of the
+// leaf, so its pairs contribute nothing (Eq. tr is truncated at r_c) and it is
+// not staged.  The leaf-pair list keeps a source leaf when the two leaves'
+// boxes come closer than r_c, so a part of each source leaf can lie farther.
+// Warp-wide box of the targets, written to the warp's two box slots in shared
+// memory (kept there, not in registers, through the item's chunk loop): each
+// lane passes the bounds of its active targets (+inf / -inf when it has none).
+// The squared cutoff is widened by a factor 1 + 2^-12: the box distance
+// computed in FP32 is a lower bound of every target's distance up to a few
+// units in the last place, and the pair loop's own cutoff test (the table's
+// zero sentinel, or x < x_c) decides each pair the kernel evaluates, so the
+// margin only keeps a few extra pairs.
+__device__ __forceinline__ void cull_box(float lox, float loy, float loz, float hix, float hiy,
+                                         float hiz, float cut, float4* __restrict__ slot)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lox = fminf(lox, __shfl_xor_sync(kFull, lox, o));
+        loy = fminf(loy, __shfl_xor_sync(kFull, loy, o));
+        loz = fminf(loz, __shfl_xor_sync(kFull, loz, o));
+        hix = fmaxf(hix, __shfl_xor_sync(kFull, hix, o));
+        hiy = fmaxf(hiy, __shfl_xor_sync(kFull, hiy, o));
+        hiz = fmaxf(hiz, __shfl_xor_sync(kFull, hiz, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slot[0] = make_float4(0.5f * (lox + hix), 0.5f * (loy + hiy), 0.5f * (loz + hiz),
+                              cut * cut * (1.0f + 1.0f / 4096.0f));
+        slot[1] = make_float4(0.5f * (hix - lox), 0.5f * (hiy - loy), 0.5f * (hiz - loz), 0.0f);
+    }
+    __syncwarp();
+}
+
+// Loads from shared memory that the compiler must not hoist or merge (the
+// target box is read at each use instead of being held in registers across
+// the staging loop, where the item's accumulators already fill them).
+__device__ __forceinline__ float4 lds_f4_v(unsigned a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+// true if the point (x, y, z) lies within the cutoff of the box kept at the
+// shared-memory address box (two float4: centre and cut^2, half extents)
+__device__ __forceinline__ bool cull_keep(unsigned box, float x, float y, float z)
+{
+    const float4 c = lds_f4_v(box), h = lds_f4_v(box + 16u);
+    const float dx = fmaxf(fabsf(x - c.x) - h.x, 0.0f);
+    const float dy = fmaxf(fabsf(y - c.y) - h.y, 0.0f);
+    const float dz = fmaxf(fabsf(z - c.z) - h.z, 0.0f);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < c.w;
+}
+
 // Per-warp shared-memory staging of a row's source particles.  Up to 32 row
 // entries are examined at once (lane k reads entry e0 + k); a warp prefix sum
-// of their leaf sizes gives each leaf's slot in the buffer, and as many whole
-// leaves as fit in `cap` slots are taken.  Each staged particle is written
-// already shifted into the target leaf's frame (its leaf offset added), so the
-// compute loop that follows is uniform over the chunk.
-constexpr int kMetaPerWarp = 32; // entries per chunk (one per lane)
+// of their leaf sizes gives each leaf's slots, and as many whole leaves as fit
+// the buffer's free slots are taken.  Each particle is shifted into the target
+// leaf's frame (its leaf offset added), tested against the target box
+// (CullBox), and the particles within the cutoff are written compacted, in
+// entry order, so the compute loop that follows is uniform over the chunk.
+// When a window of 32 entries fits whole, the next window is staged behind it,
+// so a chunk fills its buffer although the cull drops particles.
+constexpr int kMetaPerWarp = 32; // entries per window (one per lane)
+constexpr int kWarpMeta = kMetaPerWarp + 2;  // then the two CullBox slots
 
 // Stages one chunk starting at entry e0; returns the number of entries taken
-// and sets nst to the number of staged particles.  Staged coordinates are
-// multiplied by sc (the kernels' working unit per FP32 coordinate unit).
+// and sets nst to the number of staged (kept) particles.  Staged coordinates
+// are multiplied by sc (the kernels' working unit per FP32 coordinate unit).
 // MODE 0: one float4 (x, y, z, m) per particle; MODE 1: particle pairs
 // interleaved for packed arithmetic, an odd count padded with a massless
 // particle far beyond the cutoff; MODE 2 (adjoint): two float4 per particle,
@@ -121,89 +181,116 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
                                            float4* __restrict__ meta, int& nst)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned box = smem_u32(meta + kMetaPerWarp);
+    const unsigned lt = (1u << lane) - 1u;
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
-    const long long e = e0 + lane;
-    int cnt = 0, first = 0;
-    float ox = 0.f, oy = 0.f, oz = 0.f;
-    if (e < re) {
-        unsigned ent = a.pairs[e];
-        int J = (int)(ent >> 5);
-        unsigned code = ent & 31u;
-        bool ok = J < a.n_leaves && code < (unsigned)kShiftCodes;
-        int4 lj = make_int4(0, 0, 0, 0);
-        if (ok) {
-            lj = leaf[J];
-            ok = lj.x >= 0 && lj.y >= 1 && lj.y <= a.max_leaf && (long long)lj.x + lj.y <= a.n;
-        }
-        if (ok) {
-            int4 cj = lcen[J];
-            int nx, ny, nz;
-            decode_shift(code, nx, ny, nz);
-            ox = (float)(cj.x - ci.x + nx * (1 << kCentreShift)) * unit;
-            oy = (float)(cj.y - ci.y + ny * (1 << kCentreShift)) * unit;
-            oz = (float)(cj.z - ci.z + nz * (1 << kCentreShift)) * unit;
-            cnt = lj.y;
-            first = lj.x;
-        } else {
-            // a bad entry becomes one particle placed far beyond the cutoff
-            set_error(a.ctrl, kErrLeafIndex);
-            cnt = 1;
-            first = 0;
-            ox = oy = oz = 1e18f;
-        }
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const unsigned fit = __ballot_sync(kFull, e < re && incl <= cap);
-    const int ntake = __popc(fit);  // >= 1: one leaf always fits
-    nst = __shfl_sync(kFull, incl, ntake - 1);
-    const int excl = incl - cnt;
-    if (lane < ntake)
-        meta[lane] = make_float4(__int_as_float(first - excl), ox * sc, oy * sc, oz * sc);
-    __syncwarp();
-    // slot p belongs to the entry k with excl_k <= p < excl_{k+1}: count the
-    // entry starts at or before p with a position bitmask per 32-slot round
-    int C = 0;
-    for (int p0 = 0; p0 < nst + (MODE == 1 ? (nst & 1) : 0); p0 += 32) {
-        const int rel = excl - p0;
-        const unsigned bit = (lane < ntake && rel >= 0 && rel < 32) ? (1u << rel) : 0u;
-        const unsigned M = __reduce_or_sync(kFull, bit);
-        const int k = C + __popc(M & ((2u << lane) - 1u)) - 1;
-        C += __popc(M);
-        const int p = p0 + lane;
-        if (p < nst) {
-            const float4 m = meta[k];
-            const float4 v = __ldg(pf + (__float_as_int(m.x) + p));
-            if (MODE == 1) {
-                // pair j = p/2 occupies two float4: (x0, x1, y0, y1), (z0, z1, m0, m1)
-                float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + (p & 1);
-                d[0] = fmaf(v.x, sc, m.y);
-                d[2] = fmaf(v.y, sc, m.z);
-                d[4] = fmaf(v.z, sc, m.w);
-                d[6] = v.w;
-            } else if (MODE == 0) {
-                stage[p] = make_float4(fmaf(v.x, sc, m.y), fmaf(v.y, sc, m.z), fmaf(v.z, sc, m.w), v.w);
-            } else {
-                const float4 c = __ldg(reinterpret_cast<const float4*>(a.cot_sorted) +
-                                       (__float_as_int(m.x) + p));
-                stage[2 * p] = make_float4(fmaf(v.x, sc, m.y), fmaf(v.y, sc, m.z), fmaf(v.z, sc, m.w), v.w);
-                stage[2 * p + 1] = c;
+    // entries as 32-bit offsets into the row (fewer live registers)
+    const unsigned* __restrict__ prow = a.pairs + e0;
+    const int rem = (int)min(re - e0, (long long)0x7fffffff);
+    int nk = 0;  // particles kept so far
+    int eb = 0;  // entries taken so far
+    for (;;) {
+        const int e = eb + lane;
+        int cnt = 0, first = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (e < rem) {
+            unsigned ent = prow[e];
+            int J = (int)(ent >> 5);
+            unsigned code = ent & 31u;
+            bool ok = J < a.n_leaves && code < (unsigned)kShiftCodes;
+            int4 lj = make_int4(0, 0, 0, 0);
+            if (ok) {
+                lj = leaf[J];
+                ok = lj.x >= 0 && lj.y >= 1 && lj.y <= a.max_leaf && (long long)lj.x + lj.y <= a.n;
             }
-        } else if (MODE == 1 && p == nst && (nst & 1)) {
-            // pad an odd chunk with a massless particle far beyond the cutoff
-            float* d = reinterpret_cast<float*>(stage) + 8 * (p >> 1) + 1;
-            d[0] = d[2] = d[4] = 1e18f;
-            d[6] = 0.0f;
+            if (ok) {
+                int4 cj = lcen[J];
+                int nx, ny, nz;
+                decode_shift(code, nx, ny, nz);
+                ox = (float)(cj.x - ci.x + nx * (1 << kCentreShift)) * unit;
+                oy = (float)(cj.y - ci.y + ny * (1 << kCentreShift)) * unit;
+                oz = (float)(cj.z - ci.z + nz * (1 << kCentreShift)) * unit;
+                cnt = lj.y;
+                first = lj.x;
+            } else {
+                // a bad entry becomes one particle placed far beyond the cutoff
+                set_error(a.ctrl, kErrLeafIndex);
+                cnt = 1;
+                first = 0;
+                ox = oy = oz = 1e18f;
+            }
         }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned fit = __ballot_sync(kFull, e < rem && incl <= cap - nk);
+        const int ntake = __popc(fit);  // the first window takes >= 1: cap >= max_leaf
+        if (ntake == 0) break;
+        const int nraw = __shfl_sync(kFull, incl, ntake - 1);
+        const int excl = incl - cnt;
+        if (lane < ntake)
+            meta[lane] = make_float4(__int_as_float(first - excl), ox * sc, oy * sc, oz * sc);
+        __syncwarp();
+        // slot p belongs to the entry k with excl_k <= p < excl_{k+1}: count the
+        // entry starts at or before p with a position bitmask per 32-slot round
+        int C = 0;
+        for (int p0 = 0; p0 < nraw; p0 += 32) {
+            const int rel = excl - p0;
+            const unsigned bit = (lane < ntake && rel >= 0 && rel < 32) ? (1u << rel) : 0u;
+            const unsigned M = __reduce_or_sync(kFull, bit);
+            const int k = C + __popc(M & ((2u << lane) - 1u)) - 1;
+            C += __popc(M);
+            const int p = p0 + lane;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int src = 0;
+            bool keep = false;
+            if (p < nraw) {
+                const float4 m = meta[k];
+                src = __float_as_int(m.x) + p;
+                v = __ldg(pf + src);
+                v.x = fmaf(v.x, sc, m.y);
+                v.y = fmaf(v.y, sc, m.z);
+                v.z = fmaf(v.z, sc, m.w);
+                keep = cull_keep(box, v.x, v.y, v.z);
+            }
+            const unsigned K = __ballot_sync(kFull, keep);
+            const int pos = nk + __popc(K & lt);
+            if (keep) {
+                if (MODE == 1) {
+                    // pair j = pos/2 occupies two float4: (x0, x1, y0, y1), (z0, z1, m0, m1)
+                    float* d = reinterpret_cast<float*>(stage) + 8 * (pos >> 1) + (pos & 1);
+                    d[0] = v.x;
+                    d[2] = v.y;
+                    d[4] = v.z;
+                    d[6] = v.w;
+                } else if (MODE == 0) {
+                    stage[pos] = v;
+                } else {
+                    stage[2 * pos] = v;
+                    stage[2 * pos + 1] = __ldg(reinterpret_cast<const float4*>(a.cot_sorted) + src);
+                }
+            }
+            nk += __popc(K);
+        }
+        __syncwarp();
+        eb += ntake;
+        // a partly taken window means the next leaf does not fit
+        if (ntake < 32 || eb >= rem) break;
+    }
+    if (MODE == 1 && (nk & 1) && lane == 0) {
+        // pad an odd chunk with a massless particle far beyond the cutoff
+        float* d = reinterpret_cast<float*>(stage) + 8 * (nk >> 1) + 1;
+        d[0] = d[2] = d[4] = 1e18f;
+        d[6] = 0.0f;
     }
     __syncwarp();
-    return ntake;
+    nst = nk;
+    return eb;
 }
 
 // Combine the S stream partial sums of each target through shared memory
@@ -291,7 +378,13 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
         const float2 fk = fma2(t, make_float2(nmax, nmax), make_float2(kMagic, kMagic));
         const float2 ca = lds_f2((unsigned)__float_as_int(fk.x) * 8u + tab_bias);
         const float2 cb = lds_f2((unsigned)__float_as_int(fk.y) * 8u + tab_bias);
-        return fma2(t, make_float2(ca.y, cb.y), make_float2(ca.x, cb.x));
+        // Two scalar FFMAs, not one FFMA2: an f32x2 operand must sit in a
+        // register pair, and gathering (ca.y, cb.y) and (ca.x, cb.x) into pairs
+        // costs four register moves, which run on the heavy half of the FMA
+        // pipe like the f32x2 arithmetic itself (the packed kernel's limit);
+        // scalar FFMAs write their results straight into a pair and can run
+        // on either half.
+        return make_float2(fmaf(t.x, ca.y, ca.x), fmaf(t.y, cb.y, cb.x));
     } else {
         t.x = fminf(t.x, nmax);
         t.y = fminf(t.y, nmax);
@@ -345,6 +438,17 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
         ntx[r] = make_float2(-v.x * sc, -v.x * sc);
         nty[r] = make_float2(-v.y * sc, -v.y * sc);
         ntz[r] = make_float2(-v.z * sc, -v.z * sc);
+    }
+    {  // the target box for the cull (shared memory, after the entry records)
+        float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (act[r]) {
+                lx = fminf(lx, -ntx[r].x); hx = fmaxf(hx, -ntx[r].x);
+                ly = fminf(ly, -nty[r].x); hy = fmaxf(hy, -nty[r].x);
+                lz = fminf(lz, -ntz[r].x); hz = fmaxf(hz, -ntz[r].x);
+            }
+        cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
     }
     Acc3<ACC> acc[R];
     float2 fx[R], fy[R], fz[R];
@@ -455,6 +559,17 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
         xi[r].y *= sc;
         xi[r].z *= sc;
     }
+    {  // the target box for the cull (shared memory, after the entry records)
+        float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (act[r]) {
+                lx = fminf(lx, xi[r].x); hx = fmaxf(hx, xi[r].x);
+                ly = fminf(ly, xi[r].y); hy = fmaxf(hy, xi[r].y);
+                lz = fminf(lz, xi[r].z); hz = fmaxf(hz, xi[r].z);
+            }
+        cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
+    }
     Acc3<ACC> acc[R];
     float fx[R], fy[R], fz[R];
 #pragma unroll
@@ -563,7 +678,7 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
     const unsigned esize = TM == TM_TAYLOR ? 32u : TM == TM_CUBIC ? 16u : 8u;
     const size_t tab_bytes = TM == TM_EXACT ? 0 : (size_t)(a.table_n + 1) * esize;
     float4* stage = reinterpret_cast<float4*>(smem + ((tab_bytes + 15) & ~(size_t)15)) +
-                    (size_t)warp * (a.stage_cap + kMetaPerWarp);
+                    (size_t)warp * (a.stage_cap + kWarpMeta);
     float4* meta = stage + a.stage_cap;
     if (TM == TM_TAYLOR) {
         const float4* g = reinterpret_cast<const float4*>(a.table);

@@ -18,6 +18,7 @@ constexpr int kMagicBits = 0x4B400000;
 // zero term; it moves any pair farther than 1e-7 x-units by < 1e-6 relative.
 constexpr float kEps2 = 1e-20f;
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+constexpr float kInf = __builtin_huge_valf();
 
 __device__ __forceinline__ void set_error(unsigned* ctrl, unsigned bit)
 {

@@ -10,7 +10,12 @@
 // exactly those; the kernel's scratch memory - the persistent scheduler's work
 // counters and error word, and the interpolation table - lives in one
 // file-scope __device__ array of fixed size instead of in the caller's
-// workspace.  Nothing is allocated, by this library or by anything it calls.
+// workspace.  No call allocates through the runtime (no cudaMalloc, no
+// allocating library routine).  The first call on each device is the set-up:
+// it looks up the array's address (scratch_address below), and under CUDA's
+// default lazy module loading that look-up loads the module holding the array,
+// whose storage the driver allocates then; callers that cannot allow that
+// make one call per device at start-up, before any stream capture.
 #include <cuda_runtime.h>
 
 #include <mutex>

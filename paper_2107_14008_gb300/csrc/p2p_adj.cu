@@ -112,6 +112,17 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[r][i] = 0.0f;
     }
+    {  // the target box for the cull (shared memory, after the entry records)
+        float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (act[r]) {
+                lx = fminf(lx, xi[r].x); hx = fmaxf(hx, xi[r].x);
+                ly = fminf(ly, xi[r].y); hy = fmaxf(hy, xi[r].y);
+                lz = fminf(lz, xi[r].z); hz = fmaxf(hz, xi[r].z);
+            }
+        cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
+    }
     const long long re = a.rowptr[I + 1];
     long long e0 = a.rowptr[I];
     while (e0 < re) {
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
     const size_t tab_bytes = TM == TM_EXACT ? 0
                            : (size_t)(a.table_n + 1) * (TM == TM_LINEAR ? 16 : 32);
     float4* stage = reinterpret_cast<float4*>(smem + tab_bytes) +
-                    (size_t)warp * (2 * a.stage_cap + kMetaPerWarp);
+                    (size_t)warp * (2 * a.stage_cap + kWarpMeta);
     float4* meta = stage + 2 * a.stage_cap;
     if (TM != TM_EXACT) {
         const float4* g = reinterpret_cast<const float4*>(a.table);
@@ -435,7 +446,7 @@ size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 {
     size_t tab = precision != PSR_FP32_TABLE ? 0
                : (size_t)(table_n + 1) * (interp == PSR_LINEAR ? 16 : 32);
-    return tab + (size_t)warps * (2 * cap + kMetaPerWarp) * 16;
+    return tab + (size_t)warps * (2 * cap + kWarpMeta) * 16;
 }
 
 template <int TM, int ACC>

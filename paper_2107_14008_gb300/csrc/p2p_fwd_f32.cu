@@ -85,7 +85,7 @@ size_t table_entry_bytes(int interp)
 }
 
 // ---------------------------------------------------------------- launch --
-constexpr int kMetaPerWarpHost = 32;
+constexpr int kMetaPerWarpHost = 34;  // 32 entry records + 2 target-box slots
 
 size_t fwd_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 {

@@ -7,6 +7,10 @@ sqrt(sum |da|^2 / sum |a|^2)):
   FP32 paths vs exact oracle  2e-5   (spec bound)
   FP32 table vs the oracle's interpolated T of the same table: 2e-6 (what
   remains is FP32 rounding of coordinates and sums)
+  FP32 adjoint (dL/dx and dL/dm) vs the oracle gradient: 2e-5, the FP32
+  force tolerance
+Per particle, on the workloads' sampled targets: max over targets of
+|da_i| / max(|a_i|, 1e-3 rms|a|) below MAX_REL_FP32 (see there).
 """
 import numpy as np
 import pytest
@@ -27,6 +31,23 @@ def _cuda():
         pytest.skip("no CUDA device")
     from paper_2107_14008_gb300 import build
     build.build()
+
+
+# Largest per-particle error allowed on the FP32 paths.  The error of one
+# target is dominated by its closest pairs, whose FP32 coordinates (leaf-local,
+# measured from the parent cell's centre for packed leaves) round to ~1e-7 of
+# the cell size: the worst of 100 000 sampled targets of the 128^3 workload
+# measured 7.6e-5 (99th percentile 2e-6); the bound keeps a 3.3x margin.
+MAX_REL_FP32 = 2.5e-4
+
+
+def max_rel(a, ref):
+    """max_i |a_i - ref_i| / max(|ref_i|, 1e-3 rms|ref|)."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nr = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt(np.mean(nr * nr))
+    return float(np.max(np.linalg.norm(a - ref, axis=1) / np.maximum(nr, floor)))
 
 
 def rel_rms(a, ref):
@@ -271,6 +292,7 @@ def test_small_workload_all_targets():
     assert rel_rms(acc64, ref) < 1e-6
     acc32, _ = gpu_forces(b, psr.Options(precision=psr.PSR_FP32_TABLE))
     assert rel_rms(acc32, ref) < 2e-5
+    assert max_rel(acc32, ref) < MAX_REL_FP32
 
 
 @pytest.fixture(scope="module")
@@ -293,6 +315,7 @@ def test_precision_workload_sampled(precision_workload, name, kw, kernel):
     lv.check()
     assert np.all(np.isfinite(acc))
     assert rel_rms(acc[tg], ref) < 2e-5, name
+    assert max_rel(acc[tg], ref) < MAX_REL_FP32, name
 
 
 def test_precision_workload_fp64_sampled(precision_workload):
@@ -324,7 +347,7 @@ def test_adjoint_fp32_matches_oracle(case, name, kw):
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
     gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(**kw))
     lv.check()
-    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4, name
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 2e-5, name
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
 
 
@@ -367,7 +390,7 @@ def test_source_tile_sizes(kernel, tile):
     gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
     gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(source_tile=tile))
-    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 2e-5
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5
 
 
@@ -569,7 +592,7 @@ def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf):
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
     gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(accum=accum, **kw))
     lv.check()
-    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 1e-4, name
+    assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 2e-5, name
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
 
 

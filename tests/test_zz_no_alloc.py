@@ -28,12 +28,6 @@ def _cuda():
     build.build()
 
 
-def _rel_rms(a, ref):
-    a = a.double().cpu().numpy()
-    ref = ref.double().cpu().numpy()
-    return float(np.sqrt(np.sum((a - ref) ** 2) / np.sum(ref ** 2)))
-
-
 def _clustered(n=6000, L=60.0, seed=3):
     rng = np.random.default_rng(seed)
     pos, _ = synth.nfw_clustered(n, L, 0.6, 6, rng)
@@ -41,14 +35,18 @@ def _clustered(n=6000, L=60.0, seed=3):
     return pos, rng.uniform(0.2, 2.0, n), L, r_s, r_c
 
 
-@pytest.mark.parametrize("kw,tol", [
-    (dict(precision=psr.PSR_FP32_TABLE, table_n=1024, interp=psr.PSR_LINEAR), 2e-5),
-    (dict(precision=psr.PSR_FP32_TABLE, table_n=4096, interp=psr.PSR_CUBIC), 2e-5),
-    (dict(precision=psr.PSR_FP32_TABLE, kernel=psr.PSR_KERNEL_PACKED), 2e-5),
-    (dict(precision=psr.PSR_FP32_EXACT), 2e-5),
-    (dict(precision=psr.PSR_FP64), 1e-6),
+@pytest.mark.parametrize("kw", [
+    dict(precision=psr.PSR_FP32_TABLE, table_n=1024, interp=psr.PSR_LINEAR),
+    dict(precision=psr.PSR_FP32_TABLE, table_n=4096, interp=psr.PSR_CUBIC),
+    dict(precision=psr.PSR_FP32_TABLE, kernel=psr.PSR_KERNEL_PACKED),
+    dict(precision=psr.PSR_FP32_EXACT),
+    dict(precision=psr.PSR_FP64),
 ])
-def test_noalloc_matches_allocating_entry_point(kw, tol):
+def test_noalloc_matches_allocating_entry_point(kw):
+    """Both entry points launch the same kernel on the same inputs, and each
+    target's sum runs in a fixed order, so the results must be equal bit for
+    bit: a table rebuilt wrongly or counters left over from the previous call
+    would show."""
     pos, mass, L, r_s, r_c = _clustered()
     lv = psr.Leaves.build(pos, mass, L, r_s, r_c).upload()
     opts = psr.Options(**kw)
@@ -58,8 +56,7 @@ def test_noalloc_matches_allocating_entry_point(kw, tol):
         out = torch.full_like(ref, float("nan"))
         capi.psr_p2p_forces_noalloc(lv._h, opts.c(), out.data_ptr(), stream)
         torch.cuda.synchronize()
-        assert torch.isfinite(out).all()
-        assert _rel_rms(out, ref) < tol
+        assert torch.equal(out, ref)
 
 
 def test_noalloc_rejects_a_table_beyond_its_array():
