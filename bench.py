@@ -62,6 +62,12 @@ def parse():
                         "kernel, ORB leaves)")
     p.add_argument("--pm-steps", type=int, default=5,
                    help="steps of the long-range PM part on the same box (0: skip)")
+    p.add_argument("--large-steps", type=int, default=3,
+                   help="timed forward and adjoint steps of the 512^3 large workload, built on "
+                        "the GPU and validated against the oracle on sampled targets (0: skip)")
+    p.add_argument("--large-targets", type=int, default=10000,
+                   help="oracle targets that validate the large workload's forces (the adjoint "
+                        "takes a tenth of them)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
                    help="skip the precision study (one launch per T variant)")
     p.add_argument("--cpu-targets", type=int, default=100000,
@@ -168,9 +174,10 @@ PRECISION_VARIANTS = [
 ]
 
 
-def run_batch(args, psr, torch, dev, stream, flush):
+def run_batch(args, psr, torch, dev, stream, flush, check):
     """64 boxes, N log-uniform in [8^3, 64^3], L in [50, 400], half uniform and
-    half NFW-clustered, in one handle and one launch per step."""
+    half NFW-clustered, in one handle and one launch per step; with check, the
+    forces against the FP64 oracle on 200 sampled targets per box."""
     import synth
     boxes = synth.batch()
     t0 = time.perf_counter()
@@ -203,13 +210,141 @@ def run_batch(args, psr, torch, dev, stream, flush):
     lv.check()
     ms = sum(a.elapsed_time(e) for a, e in evs) / args.batch_steps
     ev = lv.evaluated_pairs
-    return {"value": ev / (ms / 1e3) / 1e9, "unit": "G pair-interactions/s", "ms_per_step": ms,
-            "boxes": len(boxes), "n": int(lv.n), "evaluated_per_step": int(ev),
+    acc = out.double().cpu().numpy()
+    cnt = torch.empty_like(out)
+    lv.forces(psr.Options(precision=best.precision, table_n=best.table_n, interp=best.interp,
+                          accum=best.accum, kernel=best.kernel, warps_per_block=best.warps_per_block,
+                          source_tile=best.source_tile, count_pairs=True), out=cnt)
+    within = lv.pair_count()
+    err = None
+    if check:
+        import numpy as np
+        import oracle
+        rng = np.random.default_rng(31)
+        num = den = 0.0
+        worst, off = 0.0, 0
+        for x in boxes:
+            tg = np.sort(rng.choice(x.n, min(200, x.n), replace=False))
+            ref, _, _ = oracle.forces(x.pos, x.mass, x.L, x.r_s, x.r_c, x.G, targets=tg, cells=True)
+            d = acc[off + tg] - ref
+            num += float(np.sum(d * d))
+            den += float(np.sum(ref * ref))
+            worst = max(worst, float(np.sqrt(np.sum(d * d) / np.sum(ref * ref))))
+            off += x.n
+        err = {"rel_rms_vs_fp64_oracle": float(np.sqrt(num / den)),
+               "worst_box_rel_rms": worst,
+               "sampled": "200 random targets per box (all of a smaller box), every box"}
+    return {"value": within / (ms / 1e3) / 1e9, "unit": "G pair-interactions/s", "ms_per_step": ms,
+            "boxes": len(boxes), "n": int(lv.n), "within_cutoff_per_step": int(within),
+            "leaf_tile_pairs_per_step": int(ev), "force_error": err,
             "host_build_s": build_s, "launch": "one persistent launch per step, CUDA graph replay",
             "tile_shape": {"kernel": "packed pairs" if best.kernel == 2 else "scalar streams",
                            "warps_per_block": best.warps_per_block,
                            "source_tile": best.source_tile},
             "path": "FP32, linear 1024 table, FP64 fold"}
+
+
+def rel_errors(a, ref):
+    """Relative RMS, and the max and 99th percentile of the per-particle
+    relative error |da_i| / max(|a_i|, 1e-3 rms|a|)."""
+    import numpy as np
+    d = a - ref
+    nr = np.linalg.norm(ref, axis=1)
+    rel = np.linalg.norm(d, axis=1) / np.maximum(nr, 1e-3 * np.sqrt(np.mean(nr * nr)))
+    return {"rel_rms": float(np.sqrt(np.sum(d * d) / np.sum(ref * ref))),
+            "max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99))}
+
+
+def run_large(args, torch, psr, dev, stream, flush, check, peak_tflops):
+    """The large workload: 512^3 particles, 70 % of the mass in 200000 NFW
+    halos, L = 1000, N_PM = 512, leaves <= 64.  The leaf set is built on the
+    GPU from device positions; FP32-table forward (the headline options) and
+    FP32 adjoint, each timed over args.large_steps steps (CUDA events, L2
+    flushed between steps); with check, forces against the FP64 oracle on
+    args.large_targets random targets and the adjoint on a tenth of them."""
+    import numpy as np
+    import synth
+    t0 = time.perf_counter()
+    b = synth.large()
+    gen_s = time.perf_counter() - t0
+    pos_d = torch.from_numpy(b.pos).to(dev)
+    mass_d = torch.from_numpy(b.mass).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lv = psr.Leaves.device_build(pos_d, mass_d, b.L, b.r_s, b.r_c, b.G, max_leaf=b.max_leaf,
+                                 fp64=False)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    del pos_d, mass_d
+    info = lv.info
+    opts = psr.Options(precision=psr.PSR_FP32_TABLE, table_n=args.table_n,
+                       interp=psr.PSR_LINEAR if args.interp == "linear" else psr.PSR_CUBIC,
+                       accum=psr.PSR_ACC_FP64 if args.accum == "fp64" else psr.PSR_ACC_KAHAN32)
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for k in range(steps):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    acc = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+    ms = timed(lambda: lv.forces(opts, out=acc), args.large_steps)
+    lv.check()
+    acc_h = acc.double().cpu().numpy()
+    lv.forces(psr.Options(precision=opts.precision, table_n=opts.table_n, interp=opts.interp,
+                          accum=opts.accum, count_pairs=True), out=acc)
+    within, kev = lv.pair_count(), lv.evaluated_count()
+    achieved = FLOPS_PER_INTERACTION * within / (ms / 1e3) / 1e12
+    cot_h = synth.cotangent(b.n, 12349)
+    cot = torch.from_numpy(cot_h).to(device=dev, dtype=torch.float32)
+    gp = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+    gm = torch.empty((b.n,), dtype=torch.float32, device=dev)
+    ms_a = timed(lambda: lv.adjoint(cot, opts, gp, gm), args.large_steps)
+    lv.check()
+    line = {"workload": "NFW-clustered 512^3, L=1000, N_PM=512, 70%% mass in %d halos, "
+                        "r_s=1.2L/N_PM, r_c=4.5r_s, leaves<=64" % b.meta.get("n_halos", 0),
+            "n": b.n, "value": within / (ms / 1e3) / 1e9,
+            "unit": "G pair-interactions/s (within the cutoff)", "ms_per_step": ms,
+            "steps": args.large_steps,
+            "within_cutoff_per_step": int(within), "kernel_evaluated_per_step": int(kev),
+            "leaf_tile_pairs_per_step": int(info.evaluated_pairs),
+            "leaves": int(info.n_leaves), "leaf_pairs": int(info.n_pairs),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "counted": "51 flops per pair within the cutoff"},
+            "device_build_ms": build_ms, "generate_s": gen_s,
+            "adjoint": {"value": within / (ms_a / 1e3) / 1e9, "ms_per_step": ms_a,
+                        "path": "FP32 adjoint (dL/dx, dL/dm), same table and pairs"},
+            "path": "leaf set built on the GPU; FP32 pair math, T from a %d-interval %s table, "
+                    "%s accumulation" % (args.table_n, args.interp, args.accum)}
+    if check:
+        import oracle
+        rng = np.random.default_rng(2025)
+        tg = np.sort(rng.choice(b.n, min(args.large_targets, b.n), replace=False))
+        t0 = time.perf_counter()
+        ref, _, _ = oracle.forces(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, targets=tg, cells=True)
+        line["force_error"] = dict(rel_errors(acc_h[tg], ref), targets=int(tg.size),
+                                   oracle_s=time.perf_counter() - t0)
+        ta = tg[::10]
+        gref, mref = oracle.adjoint(b.pos, b.mass, cot_h, b.L, b.r_s, b.r_c, b.G, targets=ta,
+                                    cells=True)
+        dg = gp.double().cpu().numpy()[ta] - gref
+        dm = gm.double().cpu().numpy()[ta] - mref
+        line["adjoint"]["rel_rms_vs_fp64_oracle_sampled"] = {
+            "targets": int(ta.size),
+            "dL_dx": float(np.sqrt(np.sum(dg * dg) / np.sum(gref * gref))),
+            "dL_dm": float(np.sqrt(np.sum(dm * dm) / np.sum(mref * mref)))}
+    del lv, acc, cot, gp, gm
+    torch.cuda.empty_cache()
+    return line
 
 
 def m2l_flops_per_entry(p):
@@ -392,7 +527,7 @@ def run_split(args, torch, psr, dev, b, opts, stream, flush, full_ms, full_evalu
     return out, totals
 
 
-def run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush, full_ms):
+def run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush, full_ms, within):
     """The paper's own design on the same workload (prior art): its
     block-per-target-leaf kernel (Algorithms 1 and 2) with the headline table
     and with its Taylor T[2] table, on the octree leaves and on the paper's
@@ -434,8 +569,9 @@ def run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush, full_ms)
         L_.check()
         ev = int(L_.info.evaluated_pairs)
         out.append({"tree": tree, "kernel": name, "ms_per_step": ms,
-                    "value": ev / (ms / 1e3) / 1e9, "unit": "G pair-interactions/s",
-                    "evaluated_pairs": ev, "slowdown_vs_headline": ms / full_ms})
+                    "value": within / (ms / 1e3) / 1e9,
+                    "unit": "G pair-interactions/s (within the cutoff)",
+                    "leaf_tile_pairs": ev, "slowdown_vs_headline": ms / full_ms})
         accs.append(acc.double().cpu().numpy())
     oi = orb.info
     line = {"orb_leaves": int(oi.n_leaves), "orb_leaf_pairs": int(oi.n_pairs),
@@ -604,9 +740,10 @@ def run_psr(args):
     # within-cutoff pairs (untimed counting run, after the timed region)
     lv.forces(psr.Options(precision=opts.precision, table_n=opts.table_n, interp=opts.interp,
                           accum=opts.accum, count_pairs=True), out=acc)
-    within = lv.pair_count()
-    evaluated = info.evaluated_pairs
-    value = world * evaluated * args.steps / (total_ms / 1e3) / 1e9
+    within = lv.pair_count()            # pairs with 0 < r < r_c: the workload's interactions
+    kernel_evaluated = lv.evaluated_count()  # pair terms the kernel computed (after its cull)
+    evaluated = info.evaluated_pairs    # all pairs of the leaf-pair tiles
+    value = world * within * args.steps / (total_ms / 1e3) / 1e9
     mean_ms = total_ms / args.steps
 
     # FP64 path beside it
@@ -628,7 +765,7 @@ def run_psr(args):
         ms64 = sum(a.elapsed_time(e) for a, e in e64) / args.fp64_steps
         ref64 = a64.cpu().numpy()
         d = acc32 - ref64
-        fp64 = {"value": evaluated / (ms64 / 1e3) / 1e9, "unit": "G pair-interactions/s",
+        fp64 = {"value": within / (ms64 / 1e3) / 1e9, "unit": "G pair-interactions/s",
                 "ms_per_step": ms64,
                 "fp32_table_rel_rms_vs_fp64_path": float(np.sqrt(np.sum(d * d) / np.sum(ref64 ** 2)))}
         # the paper's double-precision table path: FP64 pair arithmetic, T from
@@ -649,7 +786,7 @@ def run_psr(args):
         mst = sum(a.elapsed_time(e) for a, e in et) / args.fp64_steps
         dt_ = at.cpu().numpy() - ref64
         fp64["taylor4_table"] = {
-            "value": evaluated / (mst / 1e3) / 1e9, "ms_per_step": mst,
+            "value": within / (mst / 1e3) / 1e9, "ms_per_step": mst,
             "rel_rms_vs_plain_fp64_path": float(np.sqrt(np.sum(dt_ * dt_) / np.sum(ref64 ** 2))),
             "path": "FP64, T from the paper's Taylor T[4] table in FP64 (384 nodes), "
                     "1/r by Newton-Raphson from an FP32 estimate"}
@@ -674,7 +811,7 @@ def run_psr(args):
             ea.append((s0, s1))
         torch.cuda.synchronize()
         ms_a = sum(a.elapsed_time(e) for a, e in ea) / args.adjoint_steps
-        adj = {"value": evaluated / (ms_a / 1e3) / 1e9, "unit": "G pair-interactions/s",
+        adj = {"value": within / (ms_a / 1e3) / 1e9, "unit": "G pair-interactions/s",
                "ms_per_step": ms_a, "path": "FP32 adjoint (dL/dx, dL/dm), same table and pairs"}
         if args.fp64_steps > 0:
             g64, m64 = lv.adjoint(cot.double(), psr.Options(precision=psr.PSR_FP64))
@@ -711,7 +848,7 @@ def run_psr(args):
                 s1.record(stream)
                 torch.cuda.synchronize()
                 variants.append({"variant": name, "accum": accn,
-                                 "value": evaluated / (s0.elapsed_time(s1) / 1e3) / 1e9,
+                                 "value": within / (s0.elapsed_time(s1) / 1e3) / 1e9,
                                  "acc": out.double().cpu().numpy()})
         lv.check()
 
@@ -719,7 +856,8 @@ def run_psr(args):
     # replayed from a CUDA graph
     batch = None
     if args.batch_steps > 0:
-        batch = run_batch(args, psr, torch, dev, stream, flush)
+        batch = run_batch(args, psr, torch, dev, stream, flush,
+                          rank == 0 and not args.no_cpu_baseline)
 
     # end to end through the public API, host buffers, copies inside the region:
     # positions and masses from pinned host memory, leaf/pair build on the GPU
@@ -755,7 +893,7 @@ def run_psr(args):
             torch.cuda.synchronize()
             del lv3
         build_gpu_ms = (time.perf_counter() - t1) / args.e2e_steps * 1e3
-        e2e = {"value": world * evaluated / dt / 1e9, "unit": "G pair-interactions/s",
+        e2e = {"value": world * within / dt / 1e9, "unit": "G pair-interactions/s",
                "h2d_bytes_per_step": b.n * 4 * 8, "d2h_bytes_per_step": b.n * 3 * 4,
                "ms_per_step": dt * 1e3, "device_build_ms": build_gpu_ms,
                "bitwise_equal_to_device_timed_output": same,
@@ -809,12 +947,22 @@ def run_psr(args):
     paper_line = paper_acc = None
     if args.paper_steps > 0 and b.n <= (1 << 22):
         paper_line, paper_acc = run_paper_design(args, torch, psr, dev, b, lv, opts, stream, flush,
-                                                 mean_ms)
+                                                 mean_ms, within)
 
     split_line = split_acc = None
     if args.split_steps > 0 and b.n <= (1 << 22):
         split_line, split_acc = run_split(args, torch, psr, dev, b, opts, stream, flush, mean_ms,
                                           evaluated)
+
+    pk, pk_src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+
+    large_line = None
+    if args.large_steps > 0 and args.workload != "large":
+        large_line = run_large(args, torch, psr, dev, stream, flush,
+                               rank == 0 and not args.no_cpu_baseline, peak_tflops)
 
     cb = err = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -828,24 +976,19 @@ def run_psr(args):
                 for o in r_["orders"]:
                     d = split_acc[tuple(o["_key"])][tg] - ref
                     o["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+        for v in variants:
+            e_ = rel_errors(v["acc"][tg], ref)
+            v["rel_rms_vs_fp64_oracle"] = e_["rel_rms"]
+            v["max_rel_err"] = e_["max_rel"]
+            v["p99_rel_err"] = e_["p99_rel"]
     if split_line:
         for r_ in split_line["rules"]:
             for o in r_["orders"]:
                 o.pop("_key", None)
-        for v in variants:
-            d = v["acc"][tg] - ref
-            rel = np.linalg.norm(d, axis=1) / np.maximum(np.linalg.norm(ref, axis=1),
-                                                         1e-3 * np.sqrt(np.mean(np.sum(ref * ref, 1))))
-            v["rel_rms_vs_fp64_oracle"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
-            v["max_rel_err"] = float(rel.max())
-            v["p99_rel_err"] = float(np.percentile(rel, 99))
     for v in variants:
         v.pop("acc", None)
-    pk, pk_src = peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = FLOPS_PER_INTERACTION * evaluated / (mean_ms / 1e3) / 1e12
+    achieved = FLOPS_PER_INTERACTION * within / (mean_ms / 1e3) / 1e12
+    achieved_ev = FLOPS_PER_INTERACTION * kernel_evaluated / (mean_ms / 1e3) / 1e12
     clocks = clk.summary()
     line = {
         "metric": METRIC,
@@ -853,13 +996,25 @@ def run_psr(args):
         "warmup": max(3, args.warmup), "ms_per_step": mean_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(b, args),
-        "interactions": {"evaluated_per_step": evaluated, "within_cutoff_per_step": within,
-                         "within_cutoff_value": world * within * args.steps / (total_ms / 1e3) / 1e9,
+        "interactions": {"within_cutoff_per_step": within,
+                         "kernel_evaluated_per_step": kernel_evaluated,
+                         "leaf_tile_pairs_per_step": evaluated,
+                         "within_cutoff_value": value,
+                         "kernel_evaluated_value":
+                             world * kernel_evaluated * args.steps / (total_ms / 1e3) / 1e9,
+                         "leaf_tile_value": world * evaluated * args.steps / (total_ms / 1e3) / 1e9,
+                         "counts": "value and every other G/s figure count pairs with 0 < r < r_c "
+                                   "(the unit of the oracle's arm); the kernel evaluates "
+                                   "kernel_evaluated_per_step pair terms after dropping sources "
+                                   "farther than r_c from the target leaf's box, out of the "
+                                   "leaf-pair tiles' leaf_tile_pairs_per_step",
                          "leaves": int(info.n_leaves), "leaf_pairs": int(info.n_pairs),
                          "host_build_s": build_s},
         "pct_fp32_peak_51flop": 100.0 * achieved / peak_tflops,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "counted": "51 flops per pair within the cutoff",
+                     "frac_on_kernel_evaluated_pairs": achieved_ev / peak_tflops,
                      "traffic": measured_traffic() if args.workload == "precision" else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
@@ -867,13 +1022,15 @@ def run_psr(args):
         "fp64_path": fp64,
         "adjoint": adj,
         "batch": batch,
+        "large": large_line,
         "pm_long_range": pm_line,
         "fmm_operators": fmm_line,
         "split_short_range": split_line,
         "paper_design": paper_line,
         "precision_variants": variants,
         "force_error": {"rel_rms_vs_fp64_oracle": err,
-                        "sampled_targets": None if cb is None else args.cpu_targets},
+                        "sampled_targets": None if cb is None else args.cpu_targets,
+                        **({} if cb is None else rel_errors(acc32[tg], ref))},
         "e2e": e2e,
         "cpu_baseline": None if cb is None else {k: cb[k] for k in
                                                   ("value", "unit", "cores", "kind", "sample")},

@@ -303,6 +303,19 @@ int psr_autotune(psr_leaves* h, const psr_opts* base, void* d_acc, void* cuda_st
 int psr_pair_count(psr_leaves* h, void* cuda_stream, int timeout_ms, int64_t* count);
 
 /*
+ * psr_evaluated_count - host: number of pair terms the kernel of the last
+ * psr_p2p_forces call made with opts->count_pairs = 1 evaluated (target
+ * particles x source particles it ran the pair arithmetic on, self pairs
+ * included; waits up to timeout_ms for the stream).  The FP32 warp-per-leaf
+ * kernels drop staged sources that lie at least r_c from the target leaf's
+ * particle box (those pairs are zero by the truncation of Eq. tr), so their
+ * count lies between psr_pair_count's and the leaf-pair tiles' total
+ * (psr_info.evaluated_pairs); the FP64 and PSR_KERNEL_PAPER kernels evaluate
+ * every tile pair.  Errors: PSR_E_STATE, PSR_E_TIMEOUT.
+ */
+int psr_evaluated_count(psr_leaves* h, void* cuda_stream, int timeout_ms, int64_t* count);
+
+/*
  * psr_check - host: wait (at most timeout_ms) for `cuda_stream`, then read
  * and clear the workspace's device error word.  Returns PSR_E_DEVICE if a
  * kernel found an out-of-range index (the offending entry was skipped),

@@ -359,7 +359,12 @@ class Leaves:
         return Options.from_c(best), ms
 
     def pair_count(self, stream=None, timeout_ms=60000):
+        """Pairs within the cutoff counted by the last count_pairs forward."""
         return capi.psr_pair_count(self._h, _stream_handle(stream), timeout_ms)
+
+    def evaluated_count(self, stream=None, timeout_ms=60000):
+        """Pair terms the last count_pairs forward's kernel evaluated."""
+        return capi.psr_evaluated_count(self._h, _stream_handle(stream), timeout_ms)
 
     def check(self, stream=None, timeout_ms=60000):
         return capi.psr_check(self._h, _stream_handle(stream), timeout_ms)

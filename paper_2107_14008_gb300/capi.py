@@ -24,6 +24,7 @@ PSR_FMM_ACCUMULATE, PSR_FMM_F64 = 1, 2
 # every symbol include/psr.h declares
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
+           "psr_evaluated_count",
            "psr_check", "psr_table", "psr_autotune",
            "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
            "psr_device_build", "psr_device_build_finish", "psr_device_build_split",
@@ -100,6 +101,7 @@ def lib():
     L.psr_p2p_forces_noalloc.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp]
     L.psr_p2p_adjoint.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, vp, vp]
     L.psr_pair_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
+    L.psr_evaluated_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
     L.psr_autotune.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(psr_opts), ctypes.POINTER(ctypes.c_float)]
     L.psr_check.argtypes = [vp, vp, ctypes.c_int]
@@ -199,6 +201,12 @@ def psr_autotune(h, base, d_acc, stream, reps, timeout_ms):
 def psr_pair_count(h, stream, timeout_ms):
     v = ctypes.c_int64()
     check(lib().psr_pair_count(h, ctypes.c_void_p(stream), timeout_ms, ctypes.byref(v)))
+    return v.value
+
+
+def psr_evaluated_count(h, stream, timeout_ms):
+    v = ctypes.c_int64()
+    check(lib().psr_evaluated_count(h, ctypes.c_void_p(stream), timeout_ms, ctypes.byref(v)))
     return v.value
 
 

@@ -346,8 +346,8 @@ int psr_p2p_forces(psr_leaves* hh, const psr_opts* opts, void* d_acc, void* stre
     if (fwd32 && (rc = check_tile(h, a.stage_cap))) return rc;
     if ((rc = grid_blocks(h, o, 0, &a.blocks))) return rc;
     if (o.count) {
-        cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 8, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (pair counter)");
+        cudaError_t e = cudaMemsetAsync(a.ctrl + kCtrlPairsLo, 0, 16, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (pair counters)");
     }
     int e = (o.precision == PSR_FP64)          ? launch_fwd_f64(a, st)
             : (o.kernel == PSR_KERNEL_PAPER) ? launch_fwd_blk(a, o.precision, st)
@@ -457,7 +457,7 @@ int psr_autotune(psr_leaves* hh, const psr_opts* base, void* d_acc, void* stream
     return PSR_OK;
 }
 
-int psr_pair_count(psr_leaves* hh, void* stream, int timeout_ms, int64_t* count)
+static int read_counter(psr_leaves* hh, void* stream, int timeout_ms, int word, int64_t* count)
 {
     Leaves* h = reinterpret_cast<Leaves*>(hh);
     if (!h || !count) return fail(PSR_E_ARG, "null argument");
@@ -466,12 +466,22 @@ int psr_pair_count(psr_leaves* hh, void* stream, int timeout_ms, int64_t* count)
     int rc = wait_stream(st, timeout_ms);
     if (rc) return rc;
     unsigned long long v = 0;
-    cudaError_t e = cudaMemcpyAsync(&v, h->d_ws + h->lay.ctrl + kCtrlPairsLo * 4, 8,
+    cudaError_t e = cudaMemcpyAsync(&v, h->d_ws + h->lay.ctrl + word * 4, 8,
                                     cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (pair counter)");
     if ((rc = wait_stream(st, timeout_ms))) return rc;
     *count = (int64_t)v;
     return PSR_OK;
+}
+
+int psr_pair_count(psr_leaves* hh, void* stream, int timeout_ms, int64_t* count)
+{
+    return read_counter(hh, stream, timeout_ms, kCtrlPairsLo, count);
+}
+
+int psr_evaluated_count(psr_leaves* hh, void* stream, int timeout_ms, int64_t* count)
+{
+    return read_counter(hh, stream, timeout_ms, kCtrlEvalLo, count);
 }
 
 int psr_check(psr_leaves* hh, void* stream, int timeout_ms)

@@ -407,7 +407,7 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
 template <int TM, int ACC, bool COUNT, int R>
 __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             float4* __restrict__ stage, float4* __restrict__ meta,
-                                         unsigned long long& npairs)
+                                         unsigned long long& npairs, unsigned long long& nev)
 {
     const int lane = threadIdx.x & 31;
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
@@ -465,6 +465,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
     while (e0 < re) {
         int nst;
         e0 += stage_chunk<1>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (COUNT && lane == 0) nev += (unsigned long long)nst * (unsigned)nI;
         if (on) {
             const int npair = (nst + 1) >> 1;
 #pragma unroll 1
@@ -528,7 +529,8 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
 template <int TM, int ACC, bool COUNT, int R>
 __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             float4* __restrict__ stage,
-                                            float4* __restrict__ meta, unsigned long long& npairs)
+                                            float4* __restrict__ meta, unsigned long long& npairs,
+                                            unsigned long long& nev)
 {
     const int lane = threadIdx.x & 31;
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
@@ -581,6 +583,7 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
     while (e0 < re) {
         int nst;
         e0 += stage_chunk<0>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (COUNT && lane == 0) nev += (unsigned long long)nst * (unsigned)nI;
         if (on) {
             auto eval = [&](const float4 p) {
 #pragma unroll
@@ -699,7 +702,7 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
     // entry address = bits(t + 1.5*2^23) * esize + tab_bias (mod 2^32)
     const unsigned tab_bias = smem_u32(smem) - (unsigned)kMagicBits * esize;
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
-    unsigned long long npairs = 0;
+    unsigned long long npairs = 0, nev = 0;
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketFwd, 1u) * a.item_stride + a.item_offset;
@@ -718,23 +721,25 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
         }
         if (PK) {
             if (WIDE && prefer_two_per_lane(li.y))
-                fwd_item_pk<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs);
+                fwd_item_pk<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else
-                fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
+                fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
         } else {
             const int R = WIDE ? targets_per_lane(li.y, a.stage_cap) : 1;
             if (R == 3)
-                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs);
+                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else if (R == 2)
-                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs);
+                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else
-                fwd_item_sc<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs);
+                fwd_item_sc<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
         }
     }
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) npairs += __shfl_xor_sync(kFull, npairs, off);
         if (lane == 0 && npairs)
             atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlPairsLo), npairs);
+        if (lane == 0 && nev)  // lane 0 alone counted the warp's staged pairs
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlEvalLo), nev);
     }
     persistent_exit(a.ctrl + kCtrlTicketFwd, a.ctrl + kCtrlDoneFwd);
 }

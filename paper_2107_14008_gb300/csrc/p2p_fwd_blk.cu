@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
-    unsigned long long npairs = 0;
+    unsigned long long npairs = 0, nev = 0;
     for (long long b = blockIdx.x;; b += gridDim.x) {
         const long long it = b * a.item_stride + a.item_offset;
         if (it >= a.n_items) break;
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
                     }
                 }
                 since += lj.y;
+                if (COUNT) nev += (unsigned)lj.y;
                 if (since >= a.fold_every) {
                     acc.fold(fx, fy, fz);
                     since = 0;
@@ -144,6 +145,8 @@ __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
     }
     if (COUNT && npairs)
         atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlPairsLo), npairs);
+    if (COUNT && nev)
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlEvalLo), nev);
 }
 
 namespace {

@@ -54,7 +54,7 @@ __device__ __forceinline__ double rsqrt_nr(double r2)
 
 template <bool COUNT, int R, bool TAYLOR>
 __device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li, const double* tab,
-                                           unsigned long long& npairs)
+                                           unsigned long long& npairs, unsigned long long& nev)
 {
     const int lane = threadIdx.x & 31;
     const double4* __restrict__ pd = reinterpret_cast<const double4*>(a.pd);
@@ -144,6 +144,7 @@ __device__ __forceinline__ void fwd64_item(const FwdArgs& a, int I, int4 li, con
                 az[r] += w * dz;
                 if (COUNT) cnt += act[r];
             }
+            if (COUNT) nev += act[r];
         }
     }
 #pragma unroll
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(256) p2p_fwd_f64_kernel(const FwdArgs a)
     }
     const int lane = threadIdx.x & 31;
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
-    unsigned long long npairs = 0;
+    unsigned long long npairs = 0, nev = 0;
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(a.ctrl + kCtrlTicketFwd, 1u) * a.item_stride + a.item_offset;
@@ -198,14 +199,19 @@ __global__ void __launch_bounds__(256) p2p_fwd_f64_kernel(const FwdArgs a)
             continue;
         }
         if (WIDE && li.y > 32)
-            fwd64_item<COUNT, 2, TAYLOR>(a, I, li, tab, npairs);
+            fwd64_item<COUNT, 2, TAYLOR>(a, I, li, tab, npairs, nev);
         else
-            fwd64_item<COUNT, 1, TAYLOR>(a, I, li, tab, npairs);
+            fwd64_item<COUNT, 1, TAYLOR>(a, I, li, tab, npairs, nev);
     }
     if (COUNT) {
-        for (int off = 16; off > 0; off >>= 1) npairs += __shfl_xor_sync(kFull, npairs, off);
+        for (int off = 16; off > 0; off >>= 1) {
+            npairs += __shfl_xor_sync(kFull, npairs, off);
+            nev += __shfl_xor_sync(kFull, nev, off);
+        }
         if (lane == 0 && npairs)
             atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlPairsLo), npairs);
+        if (lane == 0 && nev)
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.ctrl + kCtrlEvalLo), nev);
     }
     persistent_exit(a.ctrl + kCtrlTicketFwd, a.ctrl + kCtrlDoneFwd);
 }

@@ -67,7 +67,8 @@ enum : int {
     kCtrlTicketAdj = 2,
     kCtrlDoneAdj = 3,
     kCtrlError = 8,
-    kCtrlPairsLo = 16,  // uint64 at words 16..17
+    kCtrlPairsLo = 16,  // uint64 at words 16..17: pairs within the cutoff
+    kCtrlEvalLo = 18,   // uint64 at words 18..19: pairs evaluated
     kCtrlWords = 64,
 };
 // error bits

@@ -188,6 +188,15 @@ def test_pair_count_matches_oracle(case, precision, kernel):
     # FP32 distances can move a pair within one rounding of r_c across it
     tol = 0 if precision == psr.PSR_FP64 else max(2, int(1e-6 * pairs.sum()))
     assert abs(got - int(pairs.sum())) <= tol
+    # pair terms the kernel evaluated: every leaf-tile pair for the FP64 and
+    # block-per-leaf kernels; the warp-per-leaf kernels drop sources at least
+    # r_c from the target box, so they evaluate fewer, never fewer than the
+    # pairs within the cutoff plus the self pairs
+    ev, tiles = lv.evaluated_count(), lv.evaluated_pairs
+    if precision == psr.PSR_FP64 or kernel == psr.PSR_KERNEL_PAPER:
+        assert ev == tiles
+    else:
+        assert int(pairs.sum()) + b.n <= ev <= tiles
 
 
 @pytest.mark.parametrize("interp,mode", [(psr.PSR_LINEAR, oracle.T_LINEAR),
