@@ -18,32 +18,38 @@ namespace psr {
 
 constexpr float kFourOverSqrtPi = 2.2567583341910251f;
 
-// T and Q = exp(-x^2) at table coordinate t = u - 1/2 (u = x N / x_c).
-// Linear table: one float4 (T mid, T diff, Q mid, Q diff) per interval;
-// cubic: the T and Q coefficient float4s in two arrays.  Entry N is zero.
+// T and Q' = c4 exp(-x^2) (c4 = 4/sqrt(pi) in working units).
+// Linear table: the coordinate is s = sat(r / x_c - 1/(2N)) (distances in
+// units of x_c, as in the forward kernel: the clamp to [0, 1] is folded into
+// the FMA that forms s, and rint(s N) = N, the zero entry, is beyond the
+// cutoff); one float4 (A_T, N D_T, c4 A_Q, c4 N D_Q) per interval, intercept
+// form.  Cubic: t = u - 1/2 in table units (u = x N / x_c), the T and Q
+// coefficient float4s in two arrays.  Entry N is zero.
 template <int TM>
 __device__ __forceinline__ void eval_TQ(float t, float x, float x_c, unsigned tab_bias,
-                                        unsigned q_off, float nmax, float& T, float& Q)
+                                        unsigned q_off, float nmax, float c4, float& T, float& Q)
 {
     if (TM == TM_EXACT) {
         const float q = expf(-x * x);
         const float tv = erfcf(x) + kTwoOverSqrtPi * x * q;
         const bool in = x < x_c;
         T = in ? tv : 0.0f;
-        Q = in ? q : 0.0f;
+        Q = in ? c4 * q : 0.0f;
+    } else if (TM == TM_LINEAR) {  // t = s here
+        const float fk = fmaf(t, nmax, kMagic);
+        const float4 c = lds_f4((unsigned)__float_as_int(fk) * 16u + tab_bias);
+        T = fmaf(t, c.y, c.x);
+        Q = fmaf(t, c.w, c.z);
     } else {
         t = fminf(t, nmax);
         const float fk = t + kMagic;
         const unsigned a = (unsigned)__float_as_int(fk) * 16u + tab_bias;
         const float4 c = lds_f4(a);
-        if (TM == TM_LINEAR) {  // (A_T, D_T, A_Q, D_Q): intercept form, no offset f
-            T = fmaf(t, c.y, c.x);
-            Q = fmaf(t, c.w, c.z);
-        } else {
+        {
             const float f = t - (fk - kMagic);
             const float4 d = lds_f4(a + q_off);
             T = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
-            Q = fmaf(f, fmaf(f, fmaf(f, d.w, d.z), d.y), d.x);
+            Q = c4 * fmaf(f, fmaf(f, fmaf(f, d.w, d.z), d.y), d.x);
         }
     }
 }
@@ -89,10 +95,12 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
     const BoxDev& bx = a.boxes[li.z];
     const float x_c = bx.x_c;
     const float nmax = (float)a.table_n;
-    // working unit: table intervals for the table path, x for the exact path
-    const float sc = TM == TM_EXACT ? 1.0f : (float)a.table_n / x_c;
+    // working unit: x for the exact path, x / x_c for the linear table (whose
+    // entries carry c4), table intervals for the cubic one
+    const float sc = TM == TM_EXACT ? 1.0f : TM == TM_LINEAR ? 1.0f / x_c : (float)a.table_n / x_c;
     const float xscale = 1.0f / sc;
     const float c4 = kFourOverSqrtPi / (sc * sc * sc);  // (4/sqrt(pi)) in working units
+    const float soff = -0.5f / nmax;                     // linear: s = sat(r / x_c - 1/(2N))
     const float unit = bx.unit;
     const int4 ci = lcen[I];
 
@@ -134,17 +142,15 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
                 for (int r = 0; r < R; ++r) {
                     const float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float rinv = rsqrt_ftz(r2);
+                    // the self pair and coincident pairs contribute nothing:
+                    // 1/r = 0 there makes tr3 and hh zero (T and Q stay finite)
+                    const float rinv = r2 > 0.0f ? rsqrt_ftz(r2) : 0.0f;
                     float Tv, Qv;
-                    eval_TQ<TM>(fmaf(r2, rinv, -0.5f), r2 * rinv * xscale, x_c, tab_bias, q_off,
-                                nmax, Tv, Qv);
+                    eval_TQ<TM>(TM == TM_LINEAR ? fma_sat(r2, rinv, soff) : fmaf(r2, rinv, -0.5f),
+                                r2 * rinv * xscale, x_c, tab_bias, q_off, nmax, c4, Tv, Qv);
                     const float rinv2 = rinv * rinv;
-                    float tr3 = Tv * rinv2 * rinv;                                // T/u^3
-                    float hh = -rinv2 * fmaf(3.0f, tr3, c4 * Qv);                 // g'(r)/r
-                    // the self pair and coincident pairs contribute nothing
-                    const bool nz = r2 > 0.0f;
-                    tr3 = nz ? tr3 : 0.0f;
-                    hh = nz ? hh : 0.0f;
+                    const float tr3 = Tv * rinv2 * rinv;                          // T/u^3
+                    const float hh = -rinv2 * fmaf(3.0f, tr3, Qv);                // g'(r)/r
                     const float vx = fmaf(xi[r].w, c.x, -p.w * ck[r].x);
                     const float vy = fmaf(xi[r].w, c.y, -p.w * ck[r].y);
                     const float vz = fmaf(xi[r].w, c.z, -p.w * ck[r].z);
@@ -253,8 +259,13 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
         float4* sT = reinterpret_cast<float4*>(smem);
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
             if (TM == TM_LINEAR) {
+                // (A_T, N D_T, c4 A_Q, c4 N D_Q), c4 = (4/sqrt(pi)) x_c^3: the
+                // linear path works in units of x_c (all boxes of a handle
+                // share x_c, as they share the table)
                 const float4 u = g[i], v = gq[i];
-                sT[i] = make_float4(u.z, u.y, v.z, v.y);  // (A_T, D_T, A_Q, D_Q)
+                const float n = (float)a.table_n, xc = a.boxes[0].x_c;
+                const float c4 = kFourOverSqrtPi * xc * xc * xc;
+                sT[i] = make_float4(u.z, n * u.y, c4 * v.z, c4 * n * v.y);
             } else {
                 sT[i] = g[i];
                 sT[a.table_n + 1 + i] = gq[i];
