@@ -467,11 +467,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
         e0 += stage_chunk<1>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
         if (COUNT && lane == 0) nev += (unsigned long long)nst * (unsigned)nI;
         if (on) {
-            const int npair = (nst + 1) >> 1;
-#pragma unroll 1
-            for (int k = s; k < npair; k += S) {
-                const float4 A = stage[2 * k];
-                const float4 B = stage[2 * k + 1];
+            auto evalp = [&](const float4 A, const float4 B) {
                 const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
                 const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
 #pragma unroll
@@ -494,7 +490,19 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
                         cnt += (act[r] && ub < uc && (dx.y != 0.0f || dy.y != 0.0f || dz.y != 0.0f));
                     }
                 }
+            };
+            // Two staged pairs per iteration (k and k + S, then the odd one),
+            // in the order of the plain loop: two independent dependency
+            // chains per lane, as in the scalar kernel.
+            const float4* ps = stage + 2 * s;
+            const float4* const pe = stage + 2 * ((nst + 1) >> 1);
+#pragma unroll 1
+            for (; ps + 2 * S < pe; ps += 4 * S) {
+                const float4 A0 = ps[0], B0 = ps[1], A1 = ps[2 * S], B1 = ps[2 * S + 1];
+                evalp(A0, B0);
+                evalp(A1, B1);
             }
+            if (ps < pe) evalp(ps[0], ps[1]);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 float sx = fx[r].x + fx[r].y, sy = fy[r].x + fy[r].y, sz = fz[r].x + fz[r].y;
