@@ -479,7 +479,10 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
                                          ? make_float2(fma_sat(r2.x, rinv.x, soff), fma_sat(r2.y, rinv.y, soff))
                                          : fma2(r2, rinv, mhalf);
                     const float2 Tv = eval_T2<TM>(t, r2, rinv, tab_bias, nmax, x_c, xscale);
-                    const float2 w = mul2(mul2(mul2(mul2(pm, Tv), rinv), rinv), rinv);
+                    // 1/r^3 formed beside the table lookup: two dependent
+                    // multiplies after T instead of four
+                    const float2 ri3 = mul2(mul2(rinv, rinv), rinv);
+                    const float2 w = mul2(mul2(pm, Tv), ri3);
                     fx[r] = fma2(w, dx, fx[r]);
                     fy[r] = fma2(w, dy, fy[r]);
                     fz[r] = fma2(w, dz, fz[r]);
@@ -602,7 +605,10 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
                     const float t = TM == TM_LINEAR ? fma_sat(r2, rinv, soff)
                                                     : fmaf(r2, rinv, TM == TM_TAYLOR ? 0.0f : -0.5f);
                     float Tv = eval_T1<TM>(t, r2, rinv, tab_bias, nmax, x_c, xscale);
-                    float w = p.w * Tv * rinv * rinv * rinv;
+                    // 1/r^3 formed beside the table lookup (two dependent
+                    // multiplies after T instead of four)
+                    const float ri3 = rinv * rinv * rinv;
+                    const float w = (p.w * Tv) * ri3;
                     fx[r] = fmaf(w, dx, fx[r]);
                     fy[r] = fmaf(w, dy, fy[r]);
                     fz[r] = fmaf(w, dz, fz[r]);
@@ -616,15 +622,19 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
             // Two sources per iteration (s + 2jS and s + (2j+1)S), then the odd
             // one: the same order as a plain loop over k = s, s+S, ..., with
             // half its loop and address instructions (1-3 % faster launches).
-            const float4* ps = stage + s;
-            const float4* const pe = stage + nst;
+// the loop walks 32-bit shared-window addresses (one integer add per
+            // step; 1.5 % faster than pointer arithmetic on the bench workload);
+            // the loads are volatile so that none moves across the chunk's
+            // staging stores
+            unsigned sa = smem_u32(stage + s);
+            const unsigned se = smem_u32(stage + nst), st1 = 16u * (unsigned)S;
 #pragma unroll 1
-            for (; ps + S < pe; ps += 2 * S) {
-                const float4 p0 = ps[0], p1 = ps[S];
+            for (; sa + st1 < se; sa += 2u * st1) {
+                const float4 p0 = lds_f4_v(sa), p1 = lds_f4_v(sa + st1);
                 eval(p0);
                 eval(p1);
             }
-            if (ps < pe) eval(ps[0]);
+            if (sa < se) eval(lds_f4_v(sa));
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r].fold(fx[r], fy[r], fz[r]);
         }
@@ -757,10 +767,11 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 template <int TM, int ACC, bool COUNT, bool PK>
 static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    // The scalar kernel always carries the paths of two and three targets per
-    // lane (targets_per_lane picks one per leaf).
-    auto k = (!PK || a.max_leaf > 32) ? p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>
-                                      : p2p_fwd_f32_kernel<TM, ACC, COUNT, false, PK>;
+    // Both variants always carry the two-targets-per-lane path, the scalar
+    // kernel also the three-targets path (targets_per_lane picks per leaf;
+    // the packed one takes two where prefer_two_per_lane fills more lanes:
+    // 4 % faster on the bench workload than one target per lane throughout).
+    auto k = p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -795,8 +806,7 @@ int launch_fwd_f32_variant(const FwdArgs& a, int precision, size_t smem, cudaStr
 template <bool PK>
 const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_leaf)
 {
-#define PSR_PICK(TM, ACC) ((!PK || max_leaf > 32) ? (const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK> \
-                                         : (const void*)p2p_fwd_f32_kernel<TM, ACC, false, false, PK>)
+#define PSR_PICK(TM, ACC) ((const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK>)
     if (precision == PSR_FP32_EXACT)
         return accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
     if (interp == PSR_LINEAR)
