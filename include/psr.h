@@ -110,7 +110,9 @@ typedef struct {
     int fold_every;      /* source particles summed in FP32 before a fold;
                             0 = default (64)                                  */
     int count_pairs;     /* 1: also count pairs with 0 < r < r_c (slower)     */
-    int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED | _PAPER (FP32 forward) */
+    int kernel;          /* PSR_KERNEL_AUTO | _SCALAR | _PACKED | _PAPER (FP32 forward;
+                            the FP32 adjoint runs its packed variant for
+                            _PACKED, its scalar one otherwise)               */
     int source_tile;     /* FP32 kernels: source particles staged per warp in
                             shared memory, 64 | 128 | 256 and >= the largest
                             leaf; 0 = default (forward 256, adjoint 128)    */

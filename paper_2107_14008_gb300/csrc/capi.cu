@@ -178,7 +178,7 @@ int grid_blocks(Leaves* h, const Opts& o, int adjoint, int* blocks)
         int occ = 0, e;
         if (adjoint)
             e = adj_occupancy(o.precision, o.interp, o.accum, o.warps, h->max_leaf, o.table_n,
-                              o.tile ? o.tile : kAdjStageCap, &occ);
+                              o.tile ? o.tile : kAdjStageCap, o.kernel, &occ);
         else if (o.precision == PSR_FP64)
             e = fwd_f64_occupancy(o.warps, h->max_leaf, o.interp, o.table_n, &occ);
         else if (o.kernel == PSR_KERNEL_PAPER)

@@ -173,7 +173,10 @@ constexpr int kWarpMeta = kMetaPerWarp + 2;  // then the two CullBox slots
 // MODE 0: one float4 (x, y, z, m) per particle; MODE 1: particle pairs
 // interleaved for packed arithmetic, an odd count padded with a massless
 // particle far beyond the cutoff; MODE 2 (adjoint): two float4 per particle,
-// (x, y, z, m) and the cotangent (c_x, c_y, c_z, 0) from a.cot_sorted.
+// (x, y, z, m) and the cotangent (c_x, c_y, c_z, 0) from a.cot_sorted;
+// MODE 3 (packed adjoint): particle pairs interleaved, four float4 per pair
+// (x0, x1, y0, y1), (z0, z1, m0, m1), (cx0, cx1, cy0, cy1), (cz0, cz1, 0, 0),
+// an odd count padded like MODE 1 (zero mass and cotangent).
 template <int MODE>
 __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long long re,
                                            int4 ci, float unit, float sc, int cap,
@@ -270,9 +273,20 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
                     d[6] = v.w;
                 } else if (MODE == 0) {
                     stage[pos] = v;
-                } else {
+                } else if (MODE == 2) {
                     stage[2 * pos] = v;
                     stage[2 * pos + 1] = __ldg(reinterpret_cast<const float4*>(a.cot_sorted) + src);
+                } else {
+                    const float4 c = __ldg(reinterpret_cast<const float4*>(a.cot_sorted) + src);
+                    float* d = reinterpret_cast<float*>(stage) + 16 * (pos >> 1) + (pos & 1);
+                    d[0] = v.x;
+                    d[2] = v.y;
+                    d[4] = v.z;
+                    d[6] = v.w;
+                    d[8] = c.x;
+                    d[10] = c.y;
+                    d[12] = c.z;
+                    d[14] = 0.0f;
                 }
             }
             nk += __popc(K);
@@ -287,6 +301,12 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
         float* d = reinterpret_cast<float*>(stage) + 8 * (nk >> 1) + 1;
         d[0] = d[2] = d[4] = 1e18f;
         d[6] = 0.0f;
+    }
+    if (MODE == 3 && (nk & 1) && lane == 0) {
+        // the same pad, with a zero cotangent
+        float* d = reinterpret_cast<float*>(stage) + 16 * (nk >> 1) + 1;
+        d[0] = d[2] = d[4] = 1e18f;
+        d[6] = d[8] = d[10] = d[12] = d[14] = 0.0f;
     }
     __syncwarp();
     nst = nk;

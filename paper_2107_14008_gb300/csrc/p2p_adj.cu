@@ -17,6 +17,16 @@
 namespace psr {
 
 constexpr float kFourOverSqrtPi = 2.2567583341910251f;
+constexpr float kLog2E = 1.4426950408889634f;
+
+// PTX ex2.approx.ftz.f32: one SFU instruction, 2^x with a relative error of
+// about 2^-22 (PTX ISA); the argument here is -x^2 log2(e) <= 0.
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // T and Q' = c4 exp(-x^2) (c4 = 4/sqrt(pi) in working units).
 // Linear table: the coordinate is s = sat(r / x_c - 1/(2N)) (distances in
@@ -74,6 +84,73 @@ struct Acc4 {
         }
     }
 };
+
+// Combine the S stream partials of each target and write dL/dx (scaled by
+// gx = G/(8 r_s^3) sc^3) and dL/dm (gm = -G/(4 r_s^2) sc^2) in the original
+// order.
+template <int ACC, int R>
+__device__ __forceinline__ void adj_finish(const FwdArgs& a, int4 li, Acc4<ACC>* acc,
+                                           const bool* act, int lane, int s, int q, int S, int T,
+                                           float gx, float gm, float4* __restrict__ stage)
+{
+    // Combine the S stream partials through the staging buffer: each target
+    // slot r has its own region (1 KB) and the accesses are volatile, so no
+    // slot's writes can meet another slot's reads whatever the compiler's
+    // ordering (a shared region let the second slot's stores overtake the
+    // first slot's loads).
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (ACC == PSR_ACC_FP64) {
+            volatile double* red = reinterpret_cast<volatile double*>(stage) + 128 * r;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) red[4 * lane + i] = acc[r].d[i];
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                double t4[4] = {acc[r].d[0], acc[r].d[1], acc[r].d[2], acc[r].d[3]};
+                for (int t = 1; t < S; ++t)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t4[i] += red[4 * (lane + t * T) + i];
+                const int idx = a.perm[li.x + q + T * r];
+                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                o[0] = (float)(t4[0] * (double)gx);
+                o[1] = (float)(t4[1] * (double)gx);
+                o[2] = (float)(t4[2] * (double)gx);
+                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (float)(t4[3] * (double)gm);
+            }
+        } else {
+            volatile float* red = reinterpret_cast<volatile float*>(stage) + 256 * r;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                red[8 * lane + 2 * i] = acc[r].s[i];
+                red[8 * lane + 2 * i + 1] = acc[r].c[i];
+            }
+            __syncwarp();
+            if (s == 0 && act[r]) {
+                float hi[4], lo[4], u, v;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    hi[i] = acc[r].s[i];
+                    lo[i] = acc[r].c[i];
+                }
+                for (int t = 1; t < S; ++t)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const volatile float* o = red + 8 * (lane + t * T) + 2 * i;
+                        two_sum(hi[i], o[0], u, v);
+                        hi[i] = u;
+                        lo[i] += o[1] + v;
+                    }
+                const int idx = a.perm[li.x + q + T * r];
+                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
+                o[0] = (hi[0] + lo[0]) * gx;
+                o[1] = (hi[1] + lo[1]) * gx;
+                o[2] = (hi[2] + lo[2]) * gx;
+                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (hi[3] + lo[3]) * gm;
+            }
+        }
+        __syncwarp();
+    }
+}
 
 // One target leaf on one warp (same decomposition as the forward kernels;
 // staged payload: two float4 per source particle).
@@ -178,71 +255,147 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
         }
         __syncwarp();
     }
-    // dL/dx = G/(8 r_s^3) sc^3 sum,  dL/dm = -G/(4 r_s^2) sc^2 sum
-    const float gx = bx.g_adj * sc * sc * sc;
-    const float gm = -bx.g_adjm * sc * sc;
-    // Combine the S stream partials through the staging buffer: each target
-    // slot r has its own region (1 KB) and the accesses are volatile, so no
-    // slot's writes can meet another slot's reads whatever the compiler's
-    // ordering (a shared region let the second slot's stores overtake the
-    // first slot's loads).
+    adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
+                       -bx.g_adjm * sc * sc, stage);
+}
+
+// Packed variant of adj_item (PSR_KERNEL_PACKED): each stream takes staged
+// source PAIRS and evaluates both sources of a pair at once in sm_100+ f32x2
+// arithmetic (31 of the 36 FP32 operations of a pair are vector algebra on d,
+// v and the cotangents).  The table step and 1/r stay scalar (two lookups, two
+// rsqrt); the linear path reads T alone (8-byte entries) and takes exp(-x^2)
+// from ex2, zeroed with T beyond the cutoff.  Qn carries -c4, so g'(r)/r is
+// rinv2 (-3 T/r^3 + Qn) with no negation.  Same arithmetic per pair as
+// adj_item up to rounding order.  It executes 23 % fewer instructions than
+// adj_item but is not faster: every f32x2 instruction runs on the heavy half
+// of the FMA pipe, whose load and the dependency chains of 24 warps per SM
+// hold it at about 60 % of issue.  One target per lane unless leaves exceed
+// 32 particles (the two-targets state spills at 80 registers).
+template <int TM, int ACC, int R>
+__device__ __forceinline__ void adj_item_pk(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
+                                            unsigned q_off, float4* __restrict__ stage,
+                                            float4* __restrict__ meta)
+{
+    const int lane = threadIdx.x & 31;
+    const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
+    const float4* __restrict__ cs = reinterpret_cast<const float4*>(a.cot_sorted);
+    const int4* __restrict__ lcen = reinterpret_cast<const int4*>(a.lcen);
+    const int nI = li.y;
+    const int T = (nI + R - 1) / R;
+    const int S = 32 / T;
+    const int s = lane / T;
+    const int q = lane - s * T;
+    const bool on = s < S;
+    const BoxDev& bx = a.boxes[li.z];
+    const float x_c = bx.x_c;
+    const float nmax = (float)a.table_n;
+    const float sc = TM == TM_EXACT ? 1.0f : TM == TM_LINEAR ? 1.0f / x_c : (float)a.table_n / x_c;
+    const float xscale = 1.0f / sc;
+    const float c4n = -kFourOverSqrtPi / (sc * sc * sc);  // -(4/sqrt(pi)) in working units
+    const float soff = -0.5f / nmax;
+    const float unit = bx.unit;
+    const int4 ci = lcen[I];
+
+    float2 nx[R], ny[R], nz[R], mk[R], ncx[R], ncy[R], ncz[R], fx[R], fy[R], fz[R], fm[R];
+    bool act[R];
+    Acc4<ACC> acc[R];
+    float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (ACC == PSR_ACC_FP64) {
-            volatile double* red = reinterpret_cast<volatile double*>(stage) + 128 * r;
+        const int t = q + T * r;
+        act[r] = on && t < nI;
+        const float4 v = pf[li.x + (act[r] ? t : 0)];
+        const float4 c = cs[li.x + (act[r] ? t : 0)];
+        const float x = v.x * sc, y = v.y * sc, z = v.z * sc;
+        nx[r] = make_float2(-x, -x);
+        ny[r] = make_float2(-y, -y);
+        nz[r] = make_float2(-z, -z);
+        mk[r] = make_float2(v.w, v.w);
+        ncx[r] = make_float2(-c.x, -c.x);
+        ncy[r] = make_float2(-c.y, -c.y);
+        ncz[r] = make_float2(-c.z, -c.z);
+        fx[r] = fy[r] = fz[r] = fm[r] = make_float2(0.0f, 0.0f);
+        if (act[r]) {
+            lx = fminf(lx, x); hx = fmaxf(hx, x);
+            ly = fminf(ly, y); hy = fmaxf(hy, y);
+            lz = fminf(lz, z); hz = fmaxf(hz, z);
+        }
+    }
+    cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
+    const float2 m3 = make_float2(-3.0f, -3.0f);
+    const float2 c4n2 = make_float2(c4n, c4n);
+    // exp(-x^2) = 2^(r2 qarg): r2 is in units of x_c^2 on the linear path
+    const float qarg = -kLog2E * x_c * x_c;
+    const long long re = a.rowptr[I + 1];
+    long long e0 = a.rowptr[I];
+    while (e0 < re) {
+        int nst;
+        e0 += stage_chunk<3>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
+        if (on) {
+            const int npair = (nst + 1) >> 1;
+#pragma unroll 1
+            for (int k = s; k < npair; k += S) {
+                const float4 A = stage[4 * k], B = stage[4 * k + 1];
+                const float4 C = stage[4 * k + 2], D = stage[4 * k + 3];
+                const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
+                const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
+                const float2 cx = make_float2(C.x, C.y), cy = make_float2(C.z, C.w);
+                const float2 cz = make_float2(D.x, D.y);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) red[4 * lane + i] = acc[r].d[i];
-            __syncwarp();
-            if (s == 0 && act[r]) {
-                double t4[4] = {acc[r].d[0], acc[r].d[1], acc[r].d[2], acc[r].d[3]};
-                for (int t = 1; t < S; ++t)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) t4[i] += red[4 * (lane + t * T) + i];
-                const int idx = a.perm[li.x + q + T * r];
-                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
-                o[0] = (float)(t4[0] * (double)gx);
-                o[1] = (float)(t4[1] * (double)gx);
-                o[2] = (float)(t4[2] * (double)gx);
-                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (float)(t4[3] * (double)gm);
-            }
-        } else {
-            volatile float* red = reinterpret_cast<volatile float*>(stage) + 256 * r;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                red[8 * lane + 2 * i] = acc[r].s[i];
-                red[8 * lane + 2 * i + 1] = acc[r].c[i];
-            }
-            __syncwarp();
-            if (s == 0 && act[r]) {
-                float hi[4], lo[4], u, v;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    hi[i] = acc[r].s[i];
-                    lo[i] = acc[r].c[i];
-                }
-                for (int t = 1; t < S; ++t)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const volatile float* o = red + 8 * (lane + t * T) + 2 * i;
-                        two_sum(hi[i], o[0], u, v);
-                        hi[i] = u;
-                        lo[i] += o[1] + v;
+                for (int r = 0; r < R; ++r) {
+                    const float2 dx = add2(px, nx[r]), dy = add2(py, ny[r]), dz = add2(pz, nz[r]);
+                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                    // self and coincident pairs: 1/r = 0 zeroes their terms
+                    const float2 rinv = make_float2(r2.x > 0.0f ? rsqrt_ftz(r2.x) : 0.0f,
+                                                    r2.y > 0.0f ? rsqrt_ftz(r2.y) : 0.0f);
+                    float2 Tv, Qn;
+                    if (TM == TM_LINEAR) {
+                        // T from the table (8-byte entries, as in the forward);
+                        // -c4 exp(-x^2) from ex2, zeroed with T beyond the
+                        // cutoff (the table's zero entry): half the table's
+                        // shared-memory traffic for one MUFU and three ALU
+                        // instructions per pair
+                        const float2 sv = make_float2(fma_sat(r2.x, rinv.x, soff),
+                                                      fma_sat(r2.y, rinv.y, soff));
+                        Tv = make_float2(linear_T(sv.x, nmax, tab_bias), linear_T(sv.y, nmax, tab_bias));
+                        const float2 q2 = make_float2(ex2_ftz(r2.x * qarg), ex2_ftz(r2.y * qarg));
+                        Qn = mul2(c4n2, make_float2(Tv.x > 0.0f ? q2.x : 0.0f, Tv.y > 0.0f ? q2.y : 0.0f));
+                    } else {
+                        eval_TQ<TM>(fmaf(r2.x, rinv.x, -0.5f), r2.x * rinv.x * xscale, x_c, tab_bias,
+                                    q_off, nmax, c4n, Tv.x, Qn.x);
+                        eval_TQ<TM>(fmaf(r2.y, rinv.y, -0.5f), r2.y * rinv.y * xscale, x_c, tab_bias,
+                                    q_off, nmax, c4n, Tv.y, Qn.y);
                     }
-                const int idx = a.perm[li.x + q + T * r];
-                float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
-                o[0] = (hi[0] + lo[0]) * gx;
-                o[1] = (hi[1] + lo[1]) * gx;
-                o[2] = (hi[2] + lo[2]) * gx;
-                if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (hi[3] + lo[3]) * gm;
+                    const float2 rinv2 = mul2(rinv, rinv);
+                    const float2 tr3 = mul2(Tv, mul2(rinv2, rinv));           // T/u^3
+                    const float2 hh = mul2(rinv2, fma2(m3, tr3, Qn));         // g'(r)/r
+                    const float2 vx = fma2(mk[r], cx, mul2(pm, ncx[r]));      // m_k c_j - m_j c_k
+                    const float2 vy = fma2(mk[r], cy, mul2(pm, ncy[r]));
+                    const float2 vz = fma2(mk[r], cz, mul2(pm, ncz[r]));
+                    const float2 hd = mul2(hh, fma2(dx, vx, fma2(dy, vy, mul2(dz, vz))));
+                    fx[r] = fma2(tr3, vx, fma2(hd, dx, fx[r]));
+                    fy[r] = fma2(tr3, vy, fma2(hd, dy, fy[r]));
+                    fz[r] = fma2(tr3, vz, fma2(hd, dz, fz[r]));
+                    fm[r] = fma2(tr3, fma2(dx, cx, fma2(dy, cy, mul2(dz, cz))), fm[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float f4[4] = {fx[r].x + fx[r].y, fy[r].x + fy[r].y, fz[r].x + fz[r].y,
+                               fm[r].x + fm[r].y};
+                acc[r].fold(f4);
+                fx[r] = fy[r] = fz[r] = fm[r] = make_float2(0.0f, 0.0f);
             }
         }
         __syncwarp();
     }
+    adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
+                       -bx.g_adjm * sc * sc, stage);
 }
 
 // Shared memory: the table (T and Q), then per warp a staging buffer of
 // stage_cap particles x 2 float4 plus 32 entry records.
-template <int TM, int ACC, bool WIDE>
+template <int TM, int ACC, bool WIDE, bool PK>
 __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -258,7 +411,12 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
         const float4* gq = g + (kMaxTableN + 1);
         float4* sT = reinterpret_cast<float4*>(smem);
         for (int i = threadIdx.x; i <= a.table_n; i += blockDim.x) {
-            if (TM == TM_LINEAR) {
+            if (TM == TM_LINEAR && PK) {
+                // the packed variant reads T alone, (A_T, N D_T) as in the
+                // forward kernel, and takes exp(-x^2) from ex2 (adj_item_pk)
+                const float4 u = g[i];
+                reinterpret_cast<float2*>(smem)[i] = make_float2(u.z, (float)a.table_n * u.y);
+            } else if (TM == TM_LINEAR) {
                 // (A_T, N D_T, c4 A_Q, c4 N D_Q), c4 = (4/sqrt(pi)) x_c^3: the
                 // linear path works in units of x_c (all boxes of a handle
                 // share x_c, as they share the table)
@@ -273,7 +431,7 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
         }
         __syncthreads();
     }
-    const unsigned tab_bias = smem_u32(smem) - (unsigned)kMagicBits * 16u;
+    const unsigned tab_bias = smem_u32(smem) - (unsigned)kMagicBits * (TM == TM_LINEAR && PK ? 8u : 16u);
     const unsigned q_off = (unsigned)(a.table_n + 1) * 16u;
     const int4* __restrict__ leaf = reinterpret_cast<const int4*>(a.leaf);
     for (;;) {
@@ -292,10 +450,16 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
             if (lane == 0) set_error(a.ctrl, kErrParticleRange);
             continue;
         }
-        if (WIDE && prefer_two_per_lane(li.y))
+        if (PK) {
+            if (WIDE && prefer_two_per_lane(li.y))
+                adj_item_pk<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta);
+            else
+                adj_item_pk<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
+        } else if (WIDE && prefer_two_per_lane(li.y)) {
             adj_item<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta);
-        else
+        } else {
             adj_item<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
+        }
     }
     persistent_exit(a.ctrl + kCtrlTicketAdj, a.ctrl + kCtrlDoneAdj);
 }
@@ -464,7 +628,11 @@ template <int TM, int ACC>
 static int launch_adj_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
     // always with the two-targets-per-lane path (mid-size leaves fill more lanes)
-    auto k = p2p_adj_f32_kernel<TM, ACC, true>;
+    // (the packed variant carries it only for leaves above 32 particles: its
+    // per-target state would spill)
+    auto k = a.variant != PSR_KERNEL_PACKED ? p2p_adj_f32_kernel<TM, ACC, true, false>
+             : a.max_leaf > 32              ? p2p_adj_f32_kernel<TM, ACC, true, true>
+                                            : p2p_adj_f32_kernel<TM, ACC, false, true>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -506,7 +674,7 @@ int launch_adj_f64(const FwdArgs& a, void* stream)
 }
 
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
-                  int cap, int* out)
+                  int cap, int variant, int* out)
 {
     const bool wide = max_leaf > 32;
     size_t smem = 0;
@@ -515,7 +683,10 @@ int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf,
         f = wide ? (const void*)p2p_adj_f64_kernel<true> : (const void*)p2p_adj_f64_kernel<false>;
     } else {
         smem = adj_f32_smem(precision, interp, table_n, warps, cap);
-#define PSR_PICK(TM, ACC) ((const void*)p2p_adj_f32_kernel<TM, ACC, true>)
+#define PSR_PICK(TM, ACC) (variant != PSR_KERNEL_PACKED \
+                               ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, false> \
+                               : wide ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, true> \
+                                      : (const void*)p2p_adj_f32_kernel<TM, ACC, false, true>)
         if (precision == PSR_FP32_EXACT)
             f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
         else if (interp == PSR_LINEAR)

@@ -185,7 +185,7 @@ size_t fwd_f64_smem(int interp, int table_n);
 int launch_fwd_blk(const FwdArgs& a, int precision, void* stream);  // p2p_fwd_blk.cu
 int fwd_blk_occupancy(int precision, int interp, int accum, int max_leaf, int table_n, int* out);
 int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf, int table_n,
-                  int cap, int* out);
+                  int cap, int variant, int* out);
 size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap);
 
 }  // namespace psr

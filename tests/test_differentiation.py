@@ -88,7 +88,8 @@ def test_fp64_adjoint_against_finite_differences_and_oracle(workload):
 
 @pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
 @pytest.mark.parametrize("kw", [dict(), dict(precision=psr.PSR_FP32_EXACT),
-                                dict(table_n=4096, interp=psr.PSR_CUBIC)])
+                                dict(table_n=4096, interp=psr.PSR_CUBIC),
+                                dict(kernel=psr.PSR_KERNEL_PACKED)])
 def test_fp32_adjoint_against_oracle_and_finite_differences(workload, accum, kw):
     b, cot, tg, fdx, fdm, gref, mref, aref, lv = workload
     gx, gm = lv.adjoint(torch.tensor(cot, dtype=torch.float32), psr.Options(accum=accum, **kw))

@@ -349,12 +349,13 @@ def test_adjoint_fp64_matches_oracle(case):
 
 @pytest.mark.parametrize("case", ["uniform", "clustered", "small_box"])
 @pytest.mark.parametrize("name,kw", FP32_VARIANTS)
-def test_adjoint_fp32_matches_oracle(case, name, kw):
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+def test_adjoint_fp32_matches_oracle(case, name, kw, kernel):
     b = CASES[case]()
     cot = synth.cotangent(b.n, 5)
     gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G).upload()
-    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(**kw))
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(kernel=kernel, **kw))
     lv.check()
     assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 2e-5, name
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
@@ -591,7 +592,8 @@ def test_taylor_table_is_forward_only_and_runs_without_allocation():
                                      ("exact", dict(precision=psr.PSR_FP32_EXACT))])
 @pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
 @pytest.mark.parametrize("max_leaf", [16, 64])
-def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf):
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf, kernel):
     """The FP32 adjoint's two-targets-per-lane path (leaves of 11-12 and 17-20
     particles at max_leaf 16/32, every leaf above 32 at max_leaf 64), both
     accumulations: every target slot of a lane must reduce correctly."""
@@ -599,7 +601,7 @@ def test_adjoint_fp32_two_targets_per_lane(case, name, kw, accum, max_leaf):
     cot = synth.cotangent(b.n, 6)
     gx_ref, gm_ref = oracle.adjoint(b.pos % b.L, b.mass, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
     lv = psr.Leaves.build(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
-    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(accum=accum, **kw))
+    gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(accum=accum, kernel=kernel, **kw))
     lv.check()
     assert rel_rms(gx.double().cpu().numpy(), gx_ref) < 2e-5, name
     assert rel_rms(gm.double().cpu().numpy(), gm_ref) < 2e-5, name
