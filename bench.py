@@ -1015,6 +1015,8 @@ def run_psr(args):
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "counted": "51 flops per pair within the cutoff",
                      "frac_on_kernel_evaluated_pairs": achieved_ev / peak_tflops,
+                     "frac_on_leaf_tile_pairs":
+                         FLOPS_PER_INTERACTION * evaluated / (mean_ms / 1e3) / 1e12 / peak_tflops,
                      "traffic": measured_traffic() if args.workload == "precision" else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
