@@ -3,18 +3,20 @@
 //
 // Work decomposition.  The paper gives one thread block to each target leaf
 // and one thread to each target particle, with the j-leaf staged in shared
-// memory.  Leaves here hold 1-64 particles (mean ~9 on clustered sets), so one
-// WARP takes one target leaf: each lane holds R = 1 or 2 target particles, the
-// n_I targets occupy T = ceil(n_I / R) lanes, and the warp's 32 lanes form
-// S = 32 / T streams.  The row's source leaves are staged chunk by chunk into a
-// per-warp shared-memory buffer, already shifted into the target leaf's frame,
-// and stream s takes staged particles s, s+S, ... (one broadcast shared-memory
-// load serves the T lanes of a stream).  Two variants of the inner loop:
-// scalar streams (one source per iteration) and packed pairs (two sources per
-// iteration in sm_100+ f32x2 arithmetic, half the issue slots per pair).  The
-// S partial sums of each target are combined through shared memory at the end.  Warps take target leaves
-// from an atomic ticket in largest-work-first order (persistent grid, no
-// inter-block waits).
+// memory.  Leaves here hold 1-64 particles (mean ~20 on the packed leaves of
+// clustered sets, ~9 unpacked), so one WARP takes one target leaf: each lane
+// holds R = 1, 2 or 3 target particles (chosen per leaf to fill the most
+// lanes), the n_I targets occupy T = ceil(n_I / R) lanes, and the warp's 32
+// lanes form S = 32 / T streams.  The row's source leaves are staged chunk by
+// chunk into a per-warp shared-memory buffer, already shifted into the target
+// leaf's frame and culled against the target leaf's box, and stream s takes
+// staged particles s, s+S, ... (one broadcast shared-memory load serves the T
+// lanes of a stream).  Two variants of the inner loop: scalar streams (one
+// source per iteration) and packed pairs (two sources per iteration in
+// sm_100+ f32x2 arithmetic, half the issue slots of the pair arithmetic).  The
+// S partial sums of each target are combined through shared memory at the
+// end.  Warps take target leaves from an atomic ticket in largest-work-first
+// order (persistent grid, no inter-block waits).
 //
 // Precision.  Pair arithmetic is FP32 in leaf-local coordinates scaled by
 // 1/(2 r_s); the offset between two leaf centres (with the periodic image) is
@@ -105,7 +107,8 @@ struct Acc3 {
 // leaf, so its pairs contribute nothing (Eq. tr is truncated at r_c) and it is
 // not staged.  The leaf-pair list keeps a source leaf when the two leaves'
 // boxes come closer than r_c, so a part of each source leaf can lie farther.
-// Warp-wide box of the targets, written to the warp's two box slots in shared
+//
+// cull_box: the warp-wide box of the targets, written to the warp's two box slots in shared
 // memory (kept there, not in registers, through the item's chunk loop): each
 // lane passes the bounds of its active targets (+inf / -inf when it has none).
 // The squared cutoff is widened by a factor 1 + 2^-12: the box distance
@@ -133,9 +136,12 @@ __device__ __forceinline__ void cull_box(float lox, float loy, float loz, float 
     __syncwarp();
 }
 
-// Loads from shared memory that the compiler must not hoist or merge (the
-// target box is read at each use instead of being held in registers across
-// the staging loop, where the item's accumulators already fill them).
+// Loads from shared memory that the compiler must not hoist, merge or move
+// across other volatile accesses: the target box is read at each use instead
+// of being held in registers across the staging loop (where the item's
+// accumulators already fill them), and the stream loop reads staged sources
+// through 32-bit shared addresses that must not be read before the chunk's
+// staging stores.
 __device__ __forceinline__ float4 lds_f4_v(unsigned a)
 {
     float4 v;
