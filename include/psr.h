@@ -83,7 +83,9 @@ extern "C" {
                                same pair arithmetic and tables (prior art,
                                kept for comparison)                           */
 #define PSR_KERNEL_PACKED 2 /* two source particles per lane and iteration in
-                               packed f32x2 arithmetic (sm_100+)               */
+                               packed f32x2 arithmetic (sm_100+) for leaves
+                               that take one target per lane; the scalar
+                               two- and three-targets paths for the others  */
 /* accumulation of FP32 partial sums across source leaves */
 #define PSR_ACC_FP64 0    /* fold into FP64 accumulators                    */
 #define PSR_ACC_KAHAN32 1 /* fold with compensated (two-sum) FP32           */

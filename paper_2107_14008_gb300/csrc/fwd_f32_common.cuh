@@ -13,7 +13,8 @@
 // staged particles s, s+S, ... (one broadcast shared-memory load serves the T
 // lanes of a stream).  Two variants of the inner loop: scalar streams (one
 // source per iteration) and packed pairs (two sources per iteration in
-// sm_100+ f32x2 arithmetic, half the issue slots of the pair arithmetic).  The
+// sm_100+ f32x2 arithmetic, half the issue slots of the pair arithmetic; used
+// for the leaves that take one target per lane).  The
 // S partial sums of each target are combined through shared memory at the
 // end.  Warps take target leaves from an atomic ticket in largest-work-first
 // order (persistent grid, no inter-block waits).
@@ -108,9 +109,10 @@ struct Acc3 {
 // not staged.  The leaf-pair list keeps a source leaf when the two leaves'
 // boxes come closer than r_c, so a part of each source leaf can lie farther.
 //
-// cull_box: the warp-wide box of the targets, written to the warp's two box slots in shared
-// memory (kept there, not in registers, through the item's chunk loop): each
-// lane passes the bounds of its active targets (+inf / -inf when it has none).
+// cull_box: the warp-wide box of the targets, written to the warp's two box
+// slots in shared memory (kept there, not in registers, through the item's
+// chunk loop): each lane passes the bounds of its active targets (+inf / -inf
+// when it has none).
 // The squared cutoff is widened by a factor 1 + 2^-12: the box distance
 // computed in FP32 is a lower bound of every target's distance up to a few
 // units in the last place, and the pair loop's own cutoff test (the table's
@@ -768,10 +770,18 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
             continue;
         }
         if (PK) {
-            if (WIDE && prefer_two_per_lane(li.y))
-                fwd_item_pk<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
-            else
+            // packed pairs where one target per lane fills the lanes as well
+            // as any R; elsewhere the scalar two- or three-targets paths,
+            // whose lane fill the packed state cannot reach within 64
+            // registers (10.59 against 10.78 ms for packed pairs throughout
+            // on the bench workload)
+            const int R = targets_per_lane(li.y, a.stage_cap);
+            if (R == 1)
                 fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
+            else if (R == 3)
+                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
+            else
+                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
         } else {
             const int R = WIDE ? targets_per_lane(li.y, a.stage_cap) : 1;
             if (R == 3)
@@ -797,10 +807,9 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 template <int TM, int ACC, bool COUNT, bool PK>
 static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    // Both variants always carry the two-targets-per-lane path, the scalar
-    // kernel also the three-targets path (targets_per_lane picks per leaf;
-    // the packed one takes two where prefer_two_per_lane fills more lanes:
-    // 4 % faster on the bench workload than one target per lane throughout).
+    // Both variants carry the scalar two- and three-targets-per-lane paths
+    // (targets_per_lane picks per leaf; the packed variant runs its f32x2
+    // loop for the leaves that take one target per lane).
     auto k = p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
