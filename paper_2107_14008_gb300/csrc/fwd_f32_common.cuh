@@ -181,7 +181,7 @@ constexpr int kWarpMeta = kMetaPerWarp + 2;  // then the two CullBox slots
 // MODE 0: one float4 (x, y, z, m) per particle; MODE 1: particle pairs
 // interleaved for packed arithmetic, an odd count padded with a massless
 // particle far beyond the cutoff; MODE 2 (adjoint): two float4 per particle,
-// (x, y, z, m) and the cotangent (c_x, c_y, c_z, 0) from a.cot_sorted;
+// (x, y, z, c_z) and (c_x, c_y, m, m), c the cotangent from a.cot_sorted;
 // MODE 3 (packed adjoint): particle pairs interleaved, four float4 per pair
 // (x0, x1, y0, y1), (z0, z1, m0, m1), (cx0, cx1, cy0, cy1), (cz0, cz1, 0, 0),
 // an odd count padded like MODE 1 (zero mass and cotangent).
@@ -286,8 +286,8 @@ __device__ __forceinline__ int stage_chunk(const FwdArgs& a, long long e0, long 
                 } else if (MODE == 0) {
                     stage[pos] = v;
                 } else if (MODE == 2) {
-                    stage[2 * pos] = v;
-                    stage[2 * pos + 1] = cot;
+                    stage[2 * pos] = make_float4(v.x, v.y, v.z, cot.z);
+                    stage[2 * pos + 1] = make_float4(cot.x, cot.y, v.w, v.w);
                 } else {
                     const float4 c = cot;
                     float* d = reinterpret_cast<float*>(stage) + 16 * (pos >> 1) + (pos & 1);

@@ -18,6 +18,12 @@ namespace psr {
 
 constexpr float kFourOverSqrtPi = 2.2567583341910251f;
 constexpr float kLog2E = 1.4426950408889634f;
+// Largest 1/r (in units of 1/x_c) the linear path's arithmetic takes: with
+// T <= 1 and Q <= c4, T/r^3 and (3 T/r^3 + Q)/r^2 stay finite (3 kRinvMax^5 <
+// FLT_MAX).  1/r is clamped here; only pairs closer than 2.5e-8 x_c, below
+// the resolution of the FP32 leaf-local coordinates, are affected, and at
+// r = 0 the zero table entry makes every term exactly zero.
+constexpr float kRinvMax = 4.0e7f;
 
 // PTX ex2.approx.ftz.f32: one SFU instruction, 2^x with a relative error of
 // about 2^-22 (PTX ISA); the argument here is -x^2 log2(e) <= 0.
@@ -29,11 +35,14 @@ __device__ __forceinline__ float ex2_ftz(float x)
 }
 
 // T and Q' = c4 exp(-x^2) (c4 = 4/sqrt(pi) in working units).
-// Linear table: the coordinate is s = sat(r / x_c - 1/(2N)) (distances in
-// units of x_c, as in the forward kernel: the clamp to [0, 1] is folded into
-// the FMA that forms s, and rint(s N) = N, the zero entry, is beyond the
-// cutoff); one float4 (A_T, N D_T, c4 A_Q, c4 N D_Q) per interval, intercept
-// form.  Cubic: t = u - 1/2 in table units (u = x N / x_c), the T and Q
+// Linear table: distances in units of x_c, the coordinate runs downwards,
+// s' = sat(1 + 1/(2N) - r / x_c) = 1 - s with the forward kernel's
+// s = r / x_c - 1/(2N), and rint(s' N) = N - rint(s N): entry 0 is the zero
+// entry (beyond the cutoff), entry N - k holds interval k as one float4
+// (A_T + N D_T, -N D_T, c4 (A_Q + N D_Q), -c4 N D_Q) in intercept form of s'.
+// The downward coordinate lets coincident pairs reach the zero entry for
+// free: there 1/r = +inf, r^2 (-1/r) is NaN and the saturating FMA flushes
+// NaN to 0.  Cubic: t = u - 1/2 in table units (u = x N / x_c), the T and Q
 // coefficient float4s in two arrays.  Entry N is zero.
 template <int TM>
 __device__ __forceinline__ void eval_TQ(float t, float x, float x_c, unsigned tab_bias,
@@ -152,13 +161,137 @@ __device__ __forceinline__ void adj_finish(const FwdArgs& a, int4 li, Acc4<ACC>*
     }
 }
 
+// Running sums of the two-targets-per-lane path in shared memory: the
+// register state of two targets (coordinates, cotangents, chunk partials and
+// 2 x 4 FP64 sums) does not fit the 80 registers of 3 blocks per SM, and the
+// sums, touched once per staged chunk, are the cheapest part to move out.
+// Slot (r, i), target r of the lane and component i (x, y, z, m), is the
+// 8-byte word at 256 (4 r + i) + 8 lane of the warp's accumulator block (a
+// warp's access to one slot is one conflict-free 256-byte row): one double,
+// or the compensated pair (sum, compensation).  The accesses are volatile so
+// that none is merged with or moved across another.
+constexpr int kAdjAccF4 = 128;  // accumulator block per warp (float4): 2 targets x 4 x 32 lanes x 8 B
+
+__device__ __forceinline__ unsigned acc_slot(unsigned base, int r, int i, int lane)
+{
+    return base + 256u * (unsigned)(4 * r + i) + 8u * (unsigned)lane;
+}
+
+__device__ __forceinline__ double acc_ld_f64(unsigned a)
+{
+    double d;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(d) : "r"(a) : "memory");
+    return d;
+}
+
+__device__ __forceinline__ float2 acc_ld_f2(unsigned a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+// zero the lane's R x 4 slots
+template <int R>
+__device__ __forceinline__ void acc_zero_all(unsigned base, int lane)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm volatile("st.shared.v2.f32 [%0], {%1, %1};" ::"r"(acc_slot(base, r, i, lane)),
+                         "f"(0.0f)
+                         : "memory");
+    __syncwarp();
+}
+
+// fold the lane's R x 4 chunk partials into its slots and clear them
+template <int ACC, int R>
+__device__ __forceinline__ void acc_fold_all(unsigned base, int lane, float (*f)[4])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned a = acc_slot(base, r, i, lane);
+            if (ACC == PSR_ACC_FP64) {
+                const double d = acc_ld_f64(a) + (double)f[r][i];
+                asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(d) : "memory");
+            } else {
+                const float2 v = acc_ld_f2(a);
+                float ss, ee;
+                two_sum(v.x, f[r][i], ss, ee);
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(ss), "f"(v.y + ee)
+                             : "memory");
+            }
+            f[r][i] = 0.0f;
+        }
+}
+
+// adj_finish for sums kept in shared memory: the S stream partials of each
+// target are the slots of lanes q, q + T, ..., q + (S-1) T, combined in that
+// order (the order of adj_finish).
+template <int ACC, int R>
+__device__ __forceinline__ void adj_finish_smem(const FwdArgs& a, int4 li, unsigned accb,
+                                                const bool* act, int lane, int s, int q, int S,
+                                                int T, float gx, float gm)
+{
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (s != 0 || !act[r]) continue;
+        const int idx = a.perm[li.x + q + T * r];
+        float* o = reinterpret_cast<float*>(a.out) + 3LL * idx;
+        if (ACC == PSR_ACC_FP64) {
+            double t4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) t4[i] = acc_ld_f64(acc_slot(accb, r, i, lane));
+            for (int t = 1; t < S; ++t)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t4[i] += acc_ld_f64(acc_slot(accb, r, i, lane + t * T));
+            o[0] = (float)(t4[0] * (double)gx);
+            o[1] = (float)(t4[1] * (double)gx);
+            o[2] = (float)(t4[2] * (double)gx);
+            if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (float)(t4[3] * (double)gm);
+        } else {
+            float hi[4], lo[4], u, v;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 w = acc_ld_f2(acc_slot(accb, r, i, lane));
+                hi[i] = w.x;
+                lo[i] = w.y;
+            }
+            for (int t = 1; t < S; ++t)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 w = acc_ld_f2(acc_slot(accb, r, i, lane + t * T));
+                    two_sum(hi[i], w.x, u, v);
+                    hi[i] = u;
+                    lo[i] += w.y + v;
+                }
+            o[0] = (hi[0] + lo[0]) * gx;
+            o[1] = (hi[1] + lo[1]) * gx;
+            o[2] = (hi[2] + lo[2]) * gx;
+            if (a.out_m) reinterpret_cast<float*>(a.out_m)[idx] = (hi[3] + lo[3]) * gm;
+        }
+    }
+    __syncwarp();
+}
+
 // One target leaf on one warp (same decomposition as the forward kernels;
-// staged payload: two float4 per source particle).
+// staged payload: two float4 per source particle, (x, y, z, c_z) and
+// (c_x, c_y, m, m), so that the x, y halves of d = x_j - x_k and of
+// v = m_k c_j - m_j c_k come from register pairs in f32x2 arithmetic: one
+// FADD2 and one FMUL2 + FFMA2 instead of five scalar instructions, with the
+// same rounding.  The rest of the pair stays scalar, where it spreads over
+// both halves of the FMA pipe (f32x2 runs on one).  With two targets per
+// lane the running sums live in shared memory (acc_fold_all).
 template <int TM, int ACC, int R>
 __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                          unsigned q_off, float4* __restrict__ stage,
-                                         float4* __restrict__ meta)
+                                         float4* __restrict__ meta, unsigned accb)
 {
+    constexpr bool SA = R == 2;  // sums in shared memory
     const int lane = threadIdx.x & 31;
     const float4* __restrict__ pf = reinterpret_cast<const float4*>(a.pf);
     const float4* __restrict__ cs = reinterpret_cast<const float4*>(a.cot_sorted);
@@ -177,14 +310,17 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
     const float sc = TM == TM_EXACT ? 1.0f : TM == TM_LINEAR ? 1.0f / x_c : (float)a.table_n / x_c;
     const float xscale = 1.0f / sc;
     const float c4 = kFourOverSqrtPi / (sc * sc * sc);  // (4/sqrt(pi)) in working units
-    const float soff = -0.5f / nmax;                     // linear: s = sat(r / x_c - 1/(2N))
+    const float sref = 1.0f + 0.5f / nmax;               // linear: s' = sat(1 + 1/(2N) - r / x_c)
     const float unit = bx.unit;
     const int4 ci = lcen[I];
 
-    float4 xi[R], ck[R];
+    float4 xi[R];
+    float2 nxy[R], mk2[R], nck[R];  // (-x_k, -y_k), (m_k, m_k), (-c_kx, -c_ky)
+    float nckz[R];
     bool act[R];
     float f[R][4];
-    Acc4<ACC> acc[R];
+    Acc4<ACC> acc[SA ? 1 : R];
+    if (SA) acc_zero_all<R>(accb, lane);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = q + T * r;
@@ -193,7 +329,11 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
         xi[r].x *= sc;
         xi[r].y *= sc;
         xi[r].z *= sc;
-        ck[r] = cs[li.x + (act[r] ? t : 0)];
+        const float4 ck = cs[li.x + (act[r] ? t : 0)];
+        nxy[r] = make_float2(-xi[r].x, -xi[r].y);
+        mk2[r] = make_float2(xi[r].w, xi[r].w);
+        nck[r] = make_float2(-ck.x, -ck.y);
+        nckz[r] = -ck.z;
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[r][i] = 0.0f;
     }
@@ -214,49 +354,93 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
         int nst;
         e0 += stage_chunk<2>(a, e0, re, ci, unit, sc, a.stage_cap, stage, meta, nst);
         if (on) {
+            // p = (x, y, z, c_z), c = (c_x, c_y, m, m) of one staged source
             auto eval = [&](const float4 p, const float4 c) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
+                    const float2 dxy = add2(make_float2(p.x, p.y), nxy[r]);
+                    const float dx = dxy.x, dy = dxy.y, dz = p.z - xi[r].z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     // the self pair and coincident pairs contribute nothing:
-                    // 1/r = 0 there makes tr3 and hh zero (T and Q stay finite)
-                    const float rinv = r2 > 0.0f ? rsqrt_ftz(r2) : 0.0f;
+                    // on the linear path the NaN coordinate at r = 0 selects
+                    // the zero entry (T = Q = 0) and the clamped 1/r keeps
+                    // every product finite; elsewhere 1/r = 0 makes tr3 and
+                    // hh zero (T and Q stay finite)
+                    float rinv, tv;
+                    if (TM == TM_LINEAR) {
+                        const float ri = rsqrt_ftz(r2);
+                        tv = fma_sat(r2, -ri, sref);
+                        rinv = fminf(ri, kRinvMax);
+                    } else {
+                        rinv = r2 > 0.0f ? rsqrt_ftz(r2) : 0.0f;
+                        tv = fmaf(r2, rinv, -0.5f);
+                    }
                     float Tv, Qv;
-                    eval_TQ<TM>(TM == TM_LINEAR ? fma_sat(r2, rinv, soff) : fmaf(r2, rinv, -0.5f),
-                                r2 * rinv * xscale, x_c, tab_bias, q_off, nmax, c4, Tv, Qv);
+                    eval_TQ<TM>(tv, r2 * rinv * xscale, x_c, tab_bias, q_off, nmax, c4, Tv, Qv);
                     const float rinv2 = rinv * rinv;
                     const float tr3 = Tv * rinv2 * rinv;                          // T/u^3
                     const float hh = -rinv2 * fmaf(3.0f, tr3, Qv);                // g'(r)/r
-                    const float vx = fmaf(xi[r].w, c.x, -p.w * ck[r].x);
-                    const float vy = fmaf(xi[r].w, c.y, -p.w * ck[r].y);
-                    const float vz = fmaf(xi[r].w, c.z, -p.w * ck[r].z);
+                    // v = m_k c_j - m_j c_k
+                    const float2 vxy = fma2(mk2[r], make_float2(c.x, c.y),
+                                            mul2(make_float2(c.z, c.w), nck[r]));
+                    const float vx = vxy.x, vy = vxy.y;
+                    const float vz = fmaf(xi[r].w, p.w, c.z * nckz[r]);
                     const float hd = hh * fmaf(dx, vx, fmaf(dy, vy, dz * vz));
                     f[r][0] = fmaf(tr3, vx, fmaf(hd, dx, f[r][0]));
                     f[r][1] = fmaf(tr3, vy, fmaf(hd, dy, f[r][1]));
                     f[r][2] = fmaf(tr3, vz, fmaf(hd, dz, f[r][2]));
-                    f[r][3] = fmaf(tr3, fmaf(dx, c.x, fmaf(dy, c.y, dz * c.z)), f[r][3]);
+                    f[r][3] = fmaf(tr3, fmaf(dx, c.x, fmaf(dy, c.y, dz * p.w)), f[r][3]);
                 }
             };
-            // Two staged sources per iteration (s + 2jS and s + (2j+1)S; two
-            // float4 each), then the odd one, in the order of the plain loop:
-            // 4 % faster with the FP64 fold, 9 % with the compensated one.
-            const float4* ps = stage + 2 * s;
-            const float4* const pe = stage + 2 * nst;
+            // Stream s takes staged sources s, s + S, ... in that order: four
+            // per iteration with one target per lane, two with two targets
+            // (then the rest one by one), which halves and quarters the loop
+            // instructions (the two-source loop was 4 % faster than the plain
+            // one with the FP64 fold, 9 % with the compensated one; four
+            // sources gain 0.7 % more).  The loop walks 32-bit shared
+            // addresses with volatile loads, as in the forward kernel (3 %
+            // faster than pointer arithmetic).
+            unsigned sa = smem_u32(stage + 2 * s);
+            const unsigned se = smem_u32(stage + 2 * nst), st1 = 32u * (unsigned)S;
+            if (R == 1) {
 #pragma unroll 1
-            for (; ps + 2 * S < pe; ps += 4 * S) {
-                const float4 p0 = ps[0], c0 = ps[1], p1 = ps[2 * S], c1 = ps[2 * S + 1];
-                eval(p0, c0);
-                eval(p1, c1);
+                for (; sa + 3u * st1 < se; sa += 4u * st1) {
+                    const float4 p0 = lds_f4_v(sa), c0 = lds_f4_v(sa + 16u);
+                    const float4 p1 = lds_f4_v(sa + st1), c1 = lds_f4_v(sa + st1 + 16u);
+                    const float4 p2 = lds_f4_v(sa + 2u * st1), c2 = lds_f4_v(sa + 2u * st1 + 16u);
+                    const float4 p3 = lds_f4_v(sa + 3u * st1), c3 = lds_f4_v(sa + 3u * st1 + 16u);
+                    eval(p0, c0);
+                    eval(p1, c1);
+                    eval(p2, c2);
+                    eval(p3, c3);
+                }
+#pragma unroll 1
+                for (; sa < se; sa += st1) eval(lds_f4_v(sa), lds_f4_v(sa + 16u));
+            } else {
+#pragma unroll 1
+                for (; sa + st1 < se; sa += 2u * st1) {
+                    const float4 p0 = lds_f4_v(sa), c0 = lds_f4_v(sa + 16u);
+                    const float4 p1 = lds_f4_v(sa + st1), c1 = lds_f4_v(sa + st1 + 16u);
+                    eval(p0, c0);
+                    eval(p1, c1);
+                }
+                if (sa < se) eval(lds_f4_v(sa), lds_f4_v(sa + 16u));
             }
-            if (ps < pe) eval(ps[0], ps[1]);
+            if (SA) {
+                acc_fold_all<ACC, R>(accb, lane, f);
+            } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r].fold(f[r]);
+                for (int r = 0; r < R; ++r) acc[SA ? 0 : r].fold(f[r]);
+            }
         }
         __syncwarp();
     }
-    adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
-                       -bx.g_adjm * sc * sc, stage);
+    if (SA)
+        adj_finish_smem<ACC, R>(a, li, accb, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
+                                -bx.g_adjm * sc * sc);
+    else
+        adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
+                           -bx.g_adjm * sc * sc, stage);
 }
 
 // Packed variant of adj_item (PSR_KERNEL_PACKED): each stream takes staged
@@ -394,7 +578,8 @@ __device__ __forceinline__ void adj_item_pk(const FwdArgs& a, int I, int4 li, un
 }
 
 // Shared memory: the table (T and Q), then per warp a staging buffer of
-// stage_cap particles x 2 float4 plus 32 entry records.
+// stage_cap particles x 2 float4, 32 entry records and the two box slots,
+// then the accumulator block of the two-targets path (kAdjAccF4).
 template <int TM, int ACC, bool WIDE, bool PK>
 __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
 {
@@ -404,8 +589,9 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
     const size_t tab_bytes = TM == TM_EXACT ? 0
                            : (size_t)(a.table_n + 1) * (TM == TM_LINEAR ? 16 : 32);
     float4* stage = reinterpret_cast<float4*>(smem + tab_bytes) +
-                    (size_t)warp * (2 * a.stage_cap + kWarpMeta);
+                    (size_t)warp * (2 * a.stage_cap + kWarpMeta + kAdjAccF4);
     float4* meta = stage + 2 * a.stage_cap;
+    const unsigned accb = smem_u32(meta + kWarpMeta);
     if (TM != TM_EXACT) {
         const float4* g = reinterpret_cast<const float4*>(a.table);
         const float4* gq = g + (kMaxTableN + 1);
@@ -417,13 +603,18 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
                 const float4 u = g[i];
                 reinterpret_cast<float2*>(smem)[i] = make_float2(u.z, (float)a.table_n * u.y);
             } else if (TM == TM_LINEAR) {
-                // (A_T, N D_T, c4 A_Q, c4 N D_Q), c4 = (4/sqrt(pi)) x_c^3: the
-                // linear path works in units of x_c (all boxes of a handle
-                // share x_c, as they share the table)
+                // interval i at entry N - i, in the downward coordinate s'
+                // (eval_TQ): (A_T + N D_T, -N D_T, c4 (A_Q + N D_Q), -c4 N D_Q),
+                // c4 = (4/sqrt(pi)) x_c^3 (the linear path works in units of
+                // x_c; all boxes of a handle share x_c, as they share the
+                // table); each entry is formed in FP64 and rounded once
                 const float4 u = g[i], v = gq[i];
-                const float n = (float)a.table_n, xc = a.boxes[0].x_c;
-                const float c4 = kFourOverSqrtPi * xc * xc * xc;
-                sT[i] = make_float4(u.z, n * u.y, c4 * v.z, c4 * n * v.y);
+                const double n = (double)a.table_n, xc = a.boxes[0].x_c;
+                const double c4 = 2.2567583341910251 * xc * xc * xc;
+                sT[a.table_n - i] = make_float4((float)((double)u.z + n * (double)u.y),
+                                                (float)(-n * (double)u.y),
+                                                (float)(c4 * ((double)v.z + n * (double)v.y)),
+                                                (float)(-c4 * n * (double)v.y));
             } else {
                 sT[i] = g[i];
                 sT[a.table_n + 1 + i] = gq[i];
@@ -456,9 +647,13 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
             else
                 adj_item_pk<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
         } else if (WIDE && prefer_two_per_lane(li.y)) {
-            adj_item<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta);
+            // leaves of 11-12 and 17-20 particles up to 32 (and all larger
+            // ones); at equal lane fill one target per lane is faster (its
+            // state fits the registers and its loop takes four sources per
+            // iteration): sending the ties to two targets cost 1.4 %
+            adj_item<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta, accb);
         } else {
-            adj_item<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
+            adj_item<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta, accb);
         }
     }
     persistent_exit(a.ctrl + kCtrlTicketAdj, a.ctrl + kCtrlDoneAdj);
@@ -621,7 +816,7 @@ size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap)
 {
     size_t tab = precision != PSR_FP32_TABLE ? 0
                : (size_t)(table_n + 1) * (interp == PSR_LINEAR ? 16 : 32);
-    return tab + (size_t)warps * (2 * cap + kWarpMeta) * 16;
+    return tab + (size_t)warps * (2 * cap + kWarpMeta + kAdjAccF4) * 16;
 }
 
 template <int TM, int ACC>

@@ -256,6 +256,28 @@ def test_coincident_particles_give_finite_forces():
         assert rel_rms(acc, ref) < (1e-9 if prec == psr.PSR_FP64 else 2e-5)
 
 
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+def test_coincident_particles_give_finite_adjoint(kernel):
+    """Coincident pairs contribute nothing to either gradient (r = 0: the
+    linear path's table coordinate reaches the zero entry, the others take
+    1/r = 0); every other pair of the 70 coincident particles and the 50
+    scattered ones must still match the oracle."""
+    pos = np.vstack([np.full((70, 3), 3.0), np.random.default_rng(1).random((50, 3)) * 20])
+    m = np.linspace(0.5, 1.5, 120)
+    r_s, r_c = synth.box_params(20.0, 8)
+    cot = synth.cotangent(120, 7)
+    gx_ref, gm_ref = oracle.adjoint(pos, m, cot, 20.0, r_s, r_c, 1.0, cells=True)
+    for prec in (psr.PSR_FP64, psr.PSR_FP32_TABLE, psr.PSR_FP32_EXACT):
+        lv = psr.Leaves.build(pos, m, 20.0, r_s, r_c).upload()
+        gx, gm = lv.adjoint(torch.tensor(cot), psr.Options(precision=prec, kernel=kernel))
+        lv.check()
+        gx, gm = gx.double().cpu().numpy(), gm.double().cpu().numpy()
+        assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gm))
+        tol = 1e-9 if prec == psr.PSR_FP64 else 2e-5
+        assert rel_rms(gx, gx_ref) < tol, prec
+        assert rel_rms(gm, gm_ref) < tol, prec
+
+
 def test_deterministic_and_batch_equals_single_boxes():
     boxes = [synth.small(nside=12), _clustered(n=3000), _small_box()]
     opts = psr.Options(precision=psr.PSR_FP32_TABLE)
