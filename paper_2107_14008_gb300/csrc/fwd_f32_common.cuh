@@ -568,7 +568,10 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
 }
 
 // Scalar-stream variant: stream s takes staged particles s, s+S, ... one at
-// a time (two iterations in flight per warp).
+// a time (two iterations in flight per warp).  d_x and d_y come from one
+// f32x2 add of register pairs (the staged (x, y) and the target's
+// (-x_k, -y_k)), the same rounding as two scalar subtractions: one
+// instruction fewer per pair (2 % on the 128^3 launch, 5 % at 96^3).
 template <int TM, int ACC, bool COUNT, int R>
 __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             float4* __restrict__ stage,
@@ -593,28 +596,26 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
     const float unit = bx.unit;
     const int4 ci = lcen[I];
 
-    float4 xi[R];
+    float2 nxy[R];  // (-x_k, -y_k): d_x, d_y in one f32x2 add
+    float xz[R];
     bool act[R];
+    float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int t = q + T * r;
         act[r] = on && t < nI;
-        xi[r] = pf[li.x + (act[r] ? t : 0)];
-        xi[r].x *= sc;
-        xi[r].y *= sc;
-        xi[r].z *= sc;
+        const float4 v = pf[li.x + (act[r] ? t : 0)];
+        const float x = v.x * sc, y = v.y * sc;
+        xz[r] = v.z * sc;
+        nxy[r] = make_float2(-x, -y);
+        if (act[r]) {
+            lx = fminf(lx, x); hx = fmaxf(hx, x);
+            ly = fminf(ly, y); hy = fmaxf(hy, y);
+            lz = fminf(lz, xz[r]); hz = fmaxf(hz, xz[r]);
+        }
     }
-    {  // the target box for the cull (shared memory, after the entry records)
-        float lx = kInf, ly = kInf, lz = kInf, hx = -kInf, hy = -kInf, hz = -kInf;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (act[r]) {
-                lx = fminf(lx, xi[r].x); hx = fmaxf(hx, xi[r].x);
-                ly = fminf(ly, xi[r].y); hy = fmaxf(hy, xi[r].y);
-                lz = fminf(lz, xi[r].z); hz = fmaxf(hz, xi[r].z);
-            }
-        cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
-    }
+    // the target box for the cull (shared memory, after the entry records)
+    cull_box(lx, ly, lz, hx, hy, hz, x_c * sc, meta + kMetaPerWarp);
     Acc3<ACC> acc[R];
     float fx[R], fy[R], fz[R];
 #pragma unroll
@@ -631,7 +632,8 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
             auto eval = [&](const float4 p) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    float dx = p.x - xi[r].x, dy = p.y - xi[r].y, dz = p.z - xi[r].z;
+                    const float2 dxy = add2(make_float2(p.x, p.y), nxy[r]);
+                    const float dx = dxy.x, dy = dxy.y, dz = p.z - xz[r];
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
                     float rinv = rsqrt_ftz(r2);
                     const float t = TM == TM_LINEAR ? fma_sat(r2, rinv, soff)
