@@ -70,6 +70,10 @@ def parse():
                         "takes a tenth of them)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
                    help="skip the precision study (one launch per T variant)")
+    p.add_argument("--peak-launches", type=int, default=5,
+                   help="launches of the FP32 FMA-rate microbenchmark (psr_fp32_peak); 0 skips it")
+    p.add_argument("--peak-iters", type=int, default=65536,
+                   help="iterations of 64 FMAs per thread in each microbenchmark launch")
     p.add_argument("--cpu-targets", type=int, default=100000,
                    help="targets in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -959,6 +963,22 @@ def run_psr(args):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
 
+    # the FP32 FMA rate this GPU reaches (psr_fp32_peak: independent FMA
+    # chains on every SM), beside the peak derived from the unit counts
+    fma_line = None
+    if args.peak_launches > 0:
+        sink = torch.empty(1 << 20, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        with Clocks(local) as clk_fma:
+            fma = psr.capi.psr_fp32_peak(sink.data_ptr(), sink.numel() * 4, args.peak_iters,
+                                         args.peak_launches, stream.cuda_stream, 60000)
+        del sink
+        fma_line = {"tflops": fma / 1e12, "frac_of_derived_peak": fma / 1e12 / peak_tflops,
+                    "launches": args.peak_launches,
+                    "per_thread": "8 independent FMA chains x %d steps, (SMs x 4) x 256 threads, "
+                                  "best launch" % (8 * args.peak_iters),
+                    "clocks": clk_fma.summary()}
+
     large_line = None
     if args.large_steps > 0 and args.workload != "large":
         large_line = run_large(args, torch, psr, dev, stream, flush,
@@ -993,7 +1013,8 @@ def run_psr(args):
     line = {
         "metric": METRIC,
         "value": value, "unit": "G pair-interactions/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": mean_ms, "higher_is_better": True,
+        "warmup": max(3, args.warmup), "ms_per_step": mean_ms,
+        "ms_median": statistics.median(ms), "ms_min": min(ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(b, args),
         "interactions": {"within_cutoff_per_step": within,
@@ -1020,7 +1041,10 @@ def run_psr(args):
                      "traffic": measured_traffic() if args.workload == "precision" else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_from": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
-                                  % (props.multi_processor_count, sm_max, pk_src)},
+                                  % (props.multi_processor_count, sm_max, pk_src),
+                     "frac_of_measured_fma_rate":
+                         None if fma_line is None else achieved / fma_line["tflops"]},
+        "fp32_fma_rate_measured": fma_line,
         "fp64_path": fp64,
         "adjoint": adj,
         "batch": batch,

@@ -300,6 +300,26 @@ int psr_autotune(psr_leaves* h, const psr_opts* base, void* d_acc, void* cuda_st
                  int timeout_ms, psr_opts* best, float* best_ms);
 
 /*
+ * psr_fp32_peak - host + device: measure the FP32 fused multiply-add rate
+ * of the current device, the denominator of the FP32 kernels' roofline (the
+ * paper, Section 5, states its kernel throughput as a fraction of the SP
+ * peak).  Not part of the method.  Launches `launches` times a kernel of
+ * (SMs x 4) blocks of 256 threads in which every thread runs 8 independent
+ * chains x <- x a + b (a = 0.9999, b = 1e-4: the values stay near 1) for
+ * iters x 8 steps, timing each launch with CUDA events on `cuda_stream`, and
+ * writes the best rate, 2 FLOP per FMA, to *flops_per_s.
+ *   d_sink      caller-owned device buffer of sink_bytes bytes; it receives
+ *               one float per thread (so that no chain is optimised away)
+ *               and must hold SMs x 4 x 256 floats (4 MB covers any device
+ *               of up to 1024 SMs)
+ * Synchronises the stream; every wait is bounded by timeout_ms.
+ * Errors: PSR_E_ARG (null pointer, iters or launches < 1, sink too small:
+ * the message states the size needed), PSR_E_CUDA, PSR_E_TIMEOUT.
+ */
+int psr_fp32_peak(void* d_sink, size_t sink_bytes, int iters, int launches, void* cuda_stream,
+                  int timeout_ms, double* flops_per_s);
+
+/*
  * psr_pair_count - host: number of pairs with 0 < r < r_c counted by the
  * last psr_p2p_forces call made with opts->count_pairs = 1 (waits up to
  * timeout_ms for the stream).  Errors: PSR_E_STATE, PSR_E_TIMEOUT.

@@ -25,7 +25,7 @@ PSR_FMM_ACCUMULATE, PSR_FMM_F64 = 1, 2
 EXPORTS = ["psr_build_leaves", "psr_build_leaves_batch", "psr_leaves_info", "psr_upload",
            "psr_p2p_forces", "psr_p2p_forces_noalloc", "psr_p2p_adjoint", "psr_pair_count",
            "psr_evaluated_count",
-           "psr_check", "psr_table", "psr_autotune",
+           "psr_check", "psr_table", "psr_autotune", "psr_fp32_peak",
            "psr_leaves_host_arrays", "psr_leaves_regions", "psr_device_build_scratch_bytes",
            "psr_device_build", "psr_device_build_finish", "psr_device_build_split",
            "psr_pm_create", "psr_pm_scratch_bytes", "psr_pm_forces", "psr_pm_free",
@@ -102,6 +102,8 @@ def lib():
     L.psr_p2p_adjoint.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, vp, vp]
     L.psr_pair_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
     L.psr_evaluated_count.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(i64)]
+    L.psr_fp32_peak.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                dp]
     L.psr_autotune.argtypes = [vp, ctypes.POINTER(psr_opts), vp, vp, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(psr_opts), ctypes.POINTER(ctypes.c_float)]
     L.psr_check.argtypes = [vp, vp, ctypes.c_int]
@@ -196,6 +198,13 @@ def psr_autotune(h, base, d_acc, stream, reps, timeout_ms):
     check(lib().psr_autotune(h, ctypes.byref(base), ctypes.c_void_p(d_acc), ctypes.c_void_p(stream),
                              reps, timeout_ms, ctypes.byref(best), ctypes.byref(ms)))
     return best, ms.value
+
+
+def psr_fp32_peak(d_sink, sink_bytes, iters, launches, stream, timeout_ms):
+    v = ctypes.c_double()
+    check(lib().psr_fp32_peak(ctypes.c_void_p(d_sink), sink_bytes, iters, launches,
+                              ctypes.c_void_p(stream), timeout_ms, ctypes.byref(v)))
+    return v.value
 
 
 def psr_pair_count(h, stream, timeout_ms):

@@ -457,6 +457,74 @@ int psr_autotune(psr_leaves* hh, const psr_opts* base, void* d_acc, void* stream
     return PSR_OK;
 }
 
+// ------------------------------------------------------- FP32 FMA rate --
+// Every thread runs kPeakChains independent chains x <- x a + b for iters x
+// kPeakUnroll steps and stores their sum; with a just below one the chains
+// settle near b / (1 - a) and stay normal.
+namespace {
+constexpr int kPeakChains = 8, kPeakUnroll = 8, kPeakThreads = 256, kPeakBlocksPerSm = 4;
+}
+
+__global__ void __launch_bounds__(kPeakThreads) fp32_peak_kernel(float* __restrict__ sink, int iters,
+                                                                 float a, float b)
+{
+    float x[kPeakChains];
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) x[c] = 1.0f + 1e-3f * (float)(c + (threadIdx.x & 7));
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < kPeakUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kPeakChains; ++c) x[c] = fmaf(x[c], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) s += x[c];
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int psr_fp32_peak(void* d_sink, size_t sink_bytes, int iters, int launches, void* stream,
+                  int timeout_ms, double* flops_per_s)
+{
+    if (!d_sink || !flops_per_s) return fail(PSR_E_ARG, "null argument");
+    if (iters < 1 || launches < 1) return fail(PSR_E_ARG, "iters and launches must be >= 1");
+    int dev = 0, sms = 0;
+    cudaError_t ce;
+    if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(ce, "cudaDeviceGetAttribute");
+    const int blocks = sms * kPeakBlocksPerSm;
+    const size_t need = (size_t)blocks * kPeakThreads * sizeof(float);
+    if (sink_bytes < need)
+        return fail(PSR_E_ARG, "the sink must hold " + std::to_string(need) + " bytes on this device");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((ce = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    if ((ce = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    int rc = PSR_OK;
+    float best = -1.0f;
+    for (int l = 0; l < launches && rc == PSR_OK; ++l) {
+        if ((ce = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventRecord"); break; }
+        fp32_peak_kernel<<<blocks, kPeakThreads, 0, st>>>(reinterpret_cast<float*>(d_sink), iters,
+                                                           0.9999f, 1.0e-4f);
+        if ((ce = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(ce, "FP32 peak kernel launch"); break; }
+        if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventRecord"); break; }
+        if ((rc = wait_stream(st, timeout_ms))) break;
+        float ms = 0.0f;
+        if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { rc = cuda_fail(ce, "cudaEventElapsedTime"); break; }
+        if (best < 0.0f || ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *flops_per_s = 2.0 * kPeakChains * kPeakUnroll * (double)iters * (double)blocks * kPeakThreads /
+                   ((double)best * 1e-3);
+    return PSR_OK;
+}
+
 static int read_counter(psr_leaves* hh, void* stream, int timeout_ms, int word, int64_t* count)
 {
     Leaves* h = reinterpret_cast<Leaves*>(hh);

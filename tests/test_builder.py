@@ -227,6 +227,15 @@ def test_positions_outside_box_are_wrapped():
     np.testing.assert_array_equal(a1["pairs"], a0["pairs"])
 
 
+def test_fp32_peak_rejects_bad_arguments_before_any_launch():
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_fp32_peak(0, 1 << 20, 16, 1, 0, 1000)
+    assert e.value.code == capi.PSR_E_ARG
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_fp32_peak(1 << 20, 1 << 20, 0, 1, 0, 1000)
+    assert e.value.code == capi.PSR_E_ARG
+
+
 def test_device_calls_refuse_before_upload():
     b = synth.small(nside=8)
     lv = _build(b)

@@ -716,3 +716,20 @@ def test_fp64_taylor_table_argument_rules():
     lv.forces(psr.Options(precision=psr.PSR_FP32_TABLE, interp=psr.PSR_TAYLOR4))
     a2 = lv.forces(o64).cpu().numpy()
     np.testing.assert_array_equal(a1, a2)
+
+
+def test_fp32_peak_probe_measures_a_positive_rate():
+    """psr_fp32_peak: a short run gives a finite, positive FMA rate below
+    twice the rate the unit counts allow at the device's largest clock, the
+    sink holds the chains' finite sums, and a sink too small is refused."""
+    props = torch.cuda.get_device_properties(0)
+    sink = torch.full((1 << 20,), float("nan"), dtype=torch.float32, device="cuda")
+    rate = capi.psr_fp32_peak(sink.data_ptr(), sink.numel() * 4, 64, 2, 0, 30000)
+    nominal = props.multi_processor_count * 128 * 2 * 2.5e9
+    assert 0.0 < rate < 2.0 * nominal
+    used = props.multi_processor_count * 4 * 256
+    assert torch.isfinite(sink[:used]).all()
+    with pytest.raises(capi.PsrError) as e:
+        capi.psr_fp32_peak(sink.data_ptr(), used * 4 - 4, 64, 1, 0, 30000)
+    assert e.value.code == capi.PSR_E_ARG
+
