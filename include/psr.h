@@ -152,6 +152,10 @@ typedef struct {
                                 cache, walked again by psr_device_build_finish
                                 (every row for a split or when the cache's
                                 per-row slot is below 16 runs); else 0      */
+    int equal_mass;          /* 1 if within every box all particles have one
+                                mass: the FP32 kernels then apply it once per
+                                target instead of once per pair (the paper's
+                                kernel carries a single GM, Algorithm 2)    */
 } psr_info;
 
 typedef struct psr_leaves psr_leaves; /* opaque, host-owned */

@@ -54,7 +54,7 @@ class psr_info(ctypes.Structure):
                 ("max_leaf", ctypes.c_int), ("max_row", ctypes.c_int),
                 ("build_seconds", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
                 ("n_far", ctypes.c_int64), ("theta", ctypes.c_double),
-                ("rows_walked_twice", ctypes.c_int64)]
+                ("rows_walked_twice", ctypes.c_int64), ("equal_mass", ctypes.c_int)]
 
 
 class psr_host_arrays(ctypes.Structure):

@@ -622,7 +622,17 @@ int build_batch(int nbox, const double* const* pos, const double* const* mass, c
 
         // ---- per-box constants -------------------------------------------
         h->boxdev.resize(nbox);
-        for (int b = 0; b < nbox; ++b) h->boxdev[b] = box_constants(boxes[b]);
+        h->equal_mass = true;
+        for (int b = 0; b < nbox; ++b) {
+            h->boxdev[b] = box_constants(boxes[b]);
+            // one mass for the whole box: the FP32 kernels then apply it once
+            // per target instead of once per pair
+            const int64_t f = h->box_first[b], e = h->box_first[b + 1];
+            bool eq = true;
+            for (int64_t i = f + 1; i < e && eq; ++i) eq = m[i] == m[f];
+            h->boxdev[b].m_eq = (eq && e > f) ? (float)m[f] : 0.0f;
+            if (!eq) h->equal_mass = false;
+        }
 
         // ---- sorted payloads ----------------------------------------------
         h->pf.resize((size_t)ntot * 4);

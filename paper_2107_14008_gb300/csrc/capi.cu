@@ -147,6 +147,7 @@ FwdArgs base_args(Leaves* h, const Opts& o)
     a.variant = o.kernel;
     a.item_stride = o.nshard;
     a.item_offset = o.shard;
+    a.equal_mass = h->equal_mass ? 1 : 0;
     return a;
 }
 
@@ -276,6 +277,7 @@ int psr_leaves_info(const psr_leaves* hh, psr_info* info)
     info->n_far = h->n_far;
     info->theta = h->theta;
     info->rows_walked_twice = h->device_built ? h->db_uncached : 0;
+    info->equal_mass = h->equal_mass ? 1 : 0;
     return PSR_OK;
 }
 

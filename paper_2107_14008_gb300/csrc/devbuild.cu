@@ -34,6 +34,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <thread>
 
@@ -66,7 +67,9 @@ enum : int {
     kCntError = 5,  // bit 0 non-finite input, bit 1 stack overflow, bit 2 malformed tree
     kCntFar = 6,    // well-separated (M2L) entries of the multipole split
     kCntUncached = 7,  // rows the pair cache could not hold (re-walked by the write pass)
-    kCntWords = 8,
+    kCntMassDiff = 8,  // nonzero if some particle's mass differs from particle 0's
+    kCntMass0 = 9,     // particle 0's mass (the bits of a double)
+    kCntWords = 10,
 };
 
 // The pair cache: the count walk also records each row as runs of
@@ -429,6 +432,10 @@ __global__ void k_keys(const double* __restrict__ pos, const double* __restrict_
     }
     wpos[4 * i + 3] = m;
     if (bad) atomicOr((unsigned long long*)(cnt + kCntError), 1ULL);
+    // one mass for every particle lets the FP32 kernels apply it once per target
+    const double m0 = mass ? mass[0] : 1.0 / (double)n;
+    if (m != m0) atomicOr((unsigned long long*)(cnt + kCntMassDiff), 1ULL);
+    if (i == 0) cnt[kCntMass0] = __double_as_longlong(m);
     key[i] = (spread3_d(q[0]) << 2) | (spread3_d(q[1]) << 1) | spread3_d(q[2]);
     idx[i] = (int32_t)i;
 }
@@ -1655,6 +1662,12 @@ int device_build(const double* d_pos, const double* d_mass, int64_t n, const psr
         h->theta = theta;
         h->n_far = theta > 0.0 ? c[kCntFar] : 0;
         h->boxdev = {box_constants(*box)};
+        h->equal_mass = c[kCntMassDiff] == 0;
+        if (h->equal_mass) {
+            double m0;
+            std::memcpy(&m0, &c[kCntMass0], sizeof m0);
+            h->boxdev[0].m_eq = (float)m0;
+        }
         h->lay = make_layout(*h);
     } catch (const std::bad_alloc&) {
         delete h;

@@ -436,7 +436,7 @@ __device__ __forceinline__ float2 eval_T2(float2 t, float2 r2, float2 rinv, unsi
 // per stream, S = 32 / T streams.  Each stream takes staged particle PAIRS
 // s, s+S, ... and evaluates both particles of a pair at once with packed
 // FP32 (f32x2) arithmetic.
-template <int TM, int ACC, bool COUNT, int R>
+template <int TM, int ACC, bool COUNT, bool EQM, int R>
 __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             float4* __restrict__ stage, float4* __restrict__ meta,
                                          unsigned long long& npairs, unsigned long long& nev)
@@ -514,7 +514,7 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
                     // 1/r^3 formed beside the table lookup: two dependent
                     // multiplies after T instead of four
                     const float2 ri3 = mul2(mul2(rinv, rinv), rinv);
-                    const float2 w = mul2(mul2(pm, Tv), ri3);
+                    const float2 w = EQM ? mul2(Tv, ri3) : mul2(mul2(pm, Tv), ri3);
                     fx[r] = fma2(w, dx, fx[r]);
                     fy[r] = fma2(w, dy, fy[r]);
                     fz[r] = fma2(w, dz, fz[r]);
@@ -547,7 +547,8 @@ __device__ __forceinline__ void fwd_item_pk(const FwdArgs& a, int I, int4 li, un
         }
         __syncwarp();
     }
-    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_acc * sc * sc, stage);
+    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T,
+                        bx.g_acc * sc * sc * (EQM ? bx.m_eq : 1.0f), stage);
     if (COUNT) npairs += cnt;
 }
 
@@ -572,7 +573,7 @@ __device__ __forceinline__ float eval_T1(float t, float r2, float rinv, unsigned
 // f32x2 add of register pairs (the staged (x, y) and the target's
 // (-x_k, -y_k)), the same rounding as two scalar subtractions: one
 // instruction fewer per pair (2 % on the 128^3 launch, 5 % at 96^3).
-template <int TM, int ACC, bool COUNT, int R>
+template <int TM, int ACC, bool COUNT, bool EQM, int R>
 __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             float4* __restrict__ stage,
                                             float4* __restrict__ meta, unsigned long long& npairs,
@@ -642,7 +643,7 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
                     // 1/r^3 formed beside the table lookup (two dependent
                     // multiplies after T instead of four)
                     const float ri3 = rinv * rinv * rinv;
-                    const float w = (p.w * Tv) * ri3;
+                    const float w = EQM ? Tv * ri3 : (p.w * Tv) * ri3;
                     fx[r] = fmaf(w, dx, fx[r]);
                     fy[r] = fmaf(w, dy, fy[r]);
                     fz[r] = fmaf(w, dz, fz[r]);
@@ -674,7 +675,8 @@ __device__ __forceinline__ void fwd_item_sc(const FwdArgs& a, int I, int4 li, un
         }
         __syncwarp();
     }
-    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_acc * sc * sc, stage);
+    finish_item<ACC, R>(a, li, acc, act, lane, s, q, S, T,
+                        bx.g_acc * sc * sc * (EQM ? bx.m_eq : 1.0f), stage);
     if (COUNT) npairs += cnt;
 }
 
@@ -724,7 +726,7 @@ __device__ __forceinline__ int targets_per_lane(int n, int cap)
 
 // Shared memory: the table, then one staging buffer of stage_cap particles
 // plus 32 entry records per warp.
-template <int TM, int ACC, bool COUNT, bool WIDE, bool PK>
+template <int TM, int ACC, bool COUNT, bool WIDE, bool PK, bool EQM>
 __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -779,19 +781,19 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
             // on the bench workload)
             const int R = targets_per_lane(li.y, a.stage_cap);
             if (R == 1)
-                fwd_item_pk<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_pk<TM, ACC, COUNT, EQM, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else if (R == 3)
-                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_sc<TM, ACC, COUNT, EQM, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else
-                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_sc<TM, ACC, COUNT, EQM, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
         } else {
             const int R = WIDE ? targets_per_lane(li.y, a.stage_cap) : 1;
             if (R == 3)
-                fwd_item_sc<TM, ACC, COUNT, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_sc<TM, ACC, COUNT, EQM, 3>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else if (R == 2)
-                fwd_item_sc<TM, ACC, COUNT, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_sc<TM, ACC, COUNT, EQM, 2>(a, I, li, tab_bias, stage, meta, npairs, nev);
             else
-                fwd_item_sc<TM, ACC, COUNT, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
+                fwd_item_sc<TM, ACC, COUNT, EQM, 1>(a, I, li, tab_bias, stage, meta, npairs, nev);
         }
     }
     if (COUNT) {
@@ -806,13 +808,13 @@ __global__ void __launch_bounds__(256, 4) p2p_fwd_f32_kernel(const FwdArgs a)
 
 // Launch and occupancy of the variant PK (explicitly instantiated in
 // p2p_fwd_f32_sc.cu and p2p_fwd_f32_pk.cu).
-template <int TM, int ACC, bool COUNT, bool PK>
+template <int TM, int ACC, bool COUNT, bool PK, bool EQM>
 static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
     // Both variants carry the scalar two- and three-targets-per-lane paths
     // (targets_per_lane picks per leaf; the packed variant runs its f32x2
     // loop for the leaves that take one target per lane).
-    auto k = p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK>;
+    auto k = p2p_fwd_f32_kernel<TM, ACC, COUNT, true, PK, EQM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -824,8 +826,11 @@ static int launch_t(const FwdArgs& a, size_t smem, cudaStream_t st)
 template <int TM, int ACC, bool PK>
 static int launch_c(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
-    return a.count_pairs ? launch_t<TM, ACC, true, PK>(a, smem, st)
-                         : launch_t<TM, ACC, false, PK>(a, smem, st);
+    // equal masses: the mass leaves the pair sum (the pair-counting launch,
+    // untimed, keeps the general form)
+    return a.count_pairs  ? launch_t<TM, ACC, true, PK, false>(a, smem, st)
+           : a.equal_mass ? launch_t<TM, ACC, false, PK, true>(a, smem, st)
+                          : launch_t<TM, ACC, false, PK, false>(a, smem, st);
 }
 
 template <bool PK>
@@ -847,7 +852,7 @@ int launch_fwd_f32_variant(const FwdArgs& a, int precision, size_t smem, cudaStr
 template <bool PK>
 const void* fwd_f32_kernel_ptr(int precision, int interp, int accum, int max_leaf)
 {
-#define PSR_PICK(TM, ACC) ((const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK>)
+#define PSR_PICK(TM, ACC) ((const void*)p2p_fwd_f32_kernel<TM, ACC, false, true, PK, false>)
     if (precision == PSR_FP32_EXACT)
         return accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
     if (interp == PSR_LINEAR)

@@ -286,7 +286,7 @@ __device__ __forceinline__ void adj_finish_smem(const FwdArgs& a, int4 li, unsig
 // same rounding.  The rest of the pair stays scalar, where it spreads over
 // both halves of the FMA pipe (f32x2 runs on one).  With two targets per
 // lane the running sums live in shared memory (acc_fold_all).
-template <int TM, int ACC, int R>
+template <int TM, int ACC, bool EQM, int R>
 __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                          unsigned q_off, float4* __restrict__ stage,
                                          float4* __restrict__ meta, unsigned accb)
@@ -381,10 +381,12 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
                     const float tr3 = Tv * rinv2 * rinv;                          // T/u^3
                     const float hh = -rinv2 * fmaf(3.0f, tr3, Qv);                // g'(r)/r
                     // v = m_k c_j - m_j c_k
-                    const float2 vxy = fma2(mk2[r], make_float2(c.x, c.y),
-                                            mul2(make_float2(c.z, c.w), nck[r]));
+                    // (equal masses: v = m (c_j - c_k), m applied with gx)
+                    const float2 vxy = EQM ? add2(make_float2(c.x, c.y), nck[r])
+                                           : fma2(mk2[r], make_float2(c.x, c.y),
+                                                  mul2(make_float2(c.z, c.w), nck[r]));
                     const float vx = vxy.x, vy = vxy.y;
-                    const float vz = fmaf(xi[r].w, p.w, c.z * nckz[r]);
+                    const float vz = EQM ? p.w + nckz[r] : fmaf(xi[r].w, p.w, c.z * nckz[r]);
                     const float hd = hh * fmaf(dx, vx, fmaf(dy, vy, dz * vz));
                     f[r][0] = fmaf(tr3, vx, fmaf(hd, dx, f[r][0]));
                     f[r][1] = fmaf(tr3, vy, fmaf(hd, dy, f[r][1]));
@@ -435,12 +437,11 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
         }
         __syncwarp();
     }
+    const float gx = bx.g_adj * sc * sc * sc * (EQM ? bx.m_eq : 1.0f);
     if (SA)
-        adj_finish_smem<ACC, R>(a, li, accb, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
-                                -bx.g_adjm * sc * sc);
+        adj_finish_smem<ACC, R>(a, li, accb, act, lane, s, q, S, T, gx, -bx.g_adjm * sc * sc);
     else
-        adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
-                           -bx.g_adjm * sc * sc, stage);
+        adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, gx, -bx.g_adjm * sc * sc, stage);
 }
 
 // Packed variant of adj_item (PSR_KERNEL_PACKED): each stream takes staged
@@ -455,7 +456,7 @@ __device__ __forceinline__ void adj_item(const FwdArgs& a, int I, int4 li, unsig
 // of the FMA pipe, whose load and the dependency chains of 24 warps per SM
 // hold it at about 60 % of issue.  One target per lane unless leaves exceed
 // 32 particles (the two-targets state spills at 80 registers).
-template <int TM, int ACC, int R>
+template <int TM, int ACC, bool EQM, int R>
 __device__ __forceinline__ void adj_item_pk(const FwdArgs& a, int I, int4 li, unsigned tab_bias,
                                             unsigned q_off, float4* __restrict__ stage,
                                             float4* __restrict__ meta)
@@ -553,9 +554,10 @@ __device__ __forceinline__ void adj_item_pk(const FwdArgs& a, int I, int4 li, un
                     const float2 rinv2 = mul2(rinv, rinv);
                     const float2 tr3 = mul2(Tv, mul2(rinv2, rinv));           // T/u^3
                     const float2 hh = mul2(rinv2, fma2(m3, tr3, Qn));         // g'(r)/r
-                    const float2 vx = fma2(mk[r], cx, mul2(pm, ncx[r]));      // m_k c_j - m_j c_k
-                    const float2 vy = fma2(mk[r], cy, mul2(pm, ncy[r]));
-                    const float2 vz = fma2(mk[r], cz, mul2(pm, ncz[r]));
+                    // m_k c_j - m_j c_k (equal masses: c_j - c_k, m applied with gx)
+                    const float2 vx = EQM ? add2(cx, ncx[r]) : fma2(mk[r], cx, mul2(pm, ncx[r]));
+                    const float2 vy = EQM ? add2(cy, ncy[r]) : fma2(mk[r], cy, mul2(pm, ncy[r]));
+                    const float2 vz = EQM ? add2(cz, ncz[r]) : fma2(mk[r], cz, mul2(pm, ncz[r]));
                     const float2 hd = mul2(hh, fma2(dx, vx, fma2(dy, vy, mul2(dz, vz))));
                     fx[r] = fma2(tr3, vx, fma2(hd, dx, fx[r]));
                     fy[r] = fma2(tr3, vy, fma2(hd, dy, fy[r]));
@@ -573,14 +575,14 @@ __device__ __forceinline__ void adj_item_pk(const FwdArgs& a, int I, int4 li, un
         }
         __syncwarp();
     }
-    adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T, bx.g_adj * sc * sc * sc,
-                       -bx.g_adjm * sc * sc, stage);
+    adj_finish<ACC, R>(a, li, acc, act, lane, s, q, S, T,
+                       bx.g_adj * sc * sc * sc * (EQM ? bx.m_eq : 1.0f), -bx.g_adjm * sc * sc, stage);
 }
 
 // Shared memory: the table (T and Q), then per warp a staging buffer of
 // stage_cap particles x 2 float4, 32 entry records and the two box slots,
 // then the accumulator block of the two-targets path (kAdjAccF4).
-template <int TM, int ACC, bool WIDE, bool PK>
+template <int TM, int ACC, bool WIDE, bool PK, bool EQM>
 __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -643,17 +645,17 @@ __global__ void __launch_bounds__(256, 3) p2p_adj_f32_kernel(const FwdArgs a)
         }
         if (PK) {
             if (WIDE && prefer_two_per_lane(li.y))
-                adj_item_pk<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta);
+                adj_item_pk<TM, ACC, EQM, 2>(a, I, li, tab_bias, q_off, stage, meta);
             else
-                adj_item_pk<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta);
+                adj_item_pk<TM, ACC, EQM, 1>(a, I, li, tab_bias, q_off, stage, meta);
         } else if (WIDE && prefer_two_per_lane(li.y)) {
             // leaves of 11-12 and 17-20 particles up to 32 (and all larger
             // ones); at equal lane fill one target per lane is faster (its
             // state fits the registers and its loop takes four sources per
             // iteration): sending the ties to two targets cost 1.4 %
-            adj_item<TM, ACC, 2>(a, I, li, tab_bias, q_off, stage, meta, accb);
+            adj_item<TM, ACC, EQM, 2>(a, I, li, tab_bias, q_off, stage, meta, accb);
         } else {
-            adj_item<TM, ACC, 1>(a, I, li, tab_bias, q_off, stage, meta, accb);
+            adj_item<TM, ACC, EQM, 1>(a, I, li, tab_bias, q_off, stage, meta, accb);
         }
     }
     persistent_exit(a.ctrl + kCtrlTicketAdj, a.ctrl + kCtrlDoneAdj);
@@ -819,21 +821,29 @@ size_t adj_f32_smem(int precision, int interp, int table_n, int warps, int cap)
     return tab + (size_t)warps * (2 * cap + kWarpMeta + kAdjAccF4) * 16;
 }
 
-template <int TM, int ACC>
-static int launch_adj_t(const FwdArgs& a, size_t smem, cudaStream_t st)
+template <int TM, int ACC, bool EQM>
+static int launch_adj_e(const FwdArgs& a, size_t smem, cudaStream_t st)
 {
     // always with the two-targets-per-lane path (mid-size leaves fill more lanes)
     // (the packed variant carries it only for leaves above 32 particles: its
     // per-target state would spill)
-    auto k = a.variant != PSR_KERNEL_PACKED ? p2p_adj_f32_kernel<TM, ACC, true, false>
-             : a.max_leaf > 32              ? p2p_adj_f32_kernel<TM, ACC, true, true>
-                                            : p2p_adj_f32_kernel<TM, ACC, false, true>;
+    auto k = a.variant != PSR_KERNEL_PACKED ? p2p_adj_f32_kernel<TM, ACC, true, false, EQM>
+             : a.max_leaf > 32              ? p2p_adj_f32_kernel<TM, ACC, true, true, EQM>
+                                            : p2p_adj_f32_kernel<TM, ACC, false, true, EQM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
     }
     k<<<a.blocks, a.warps_per_block * 32, smem, st>>>(a);
     return (int)cudaGetLastError();
+}
+
+// equal masses: m leaves the pair sums (v = m (c_j - c_k))
+template <int TM, int ACC>
+static int launch_adj_t(const FwdArgs& a, size_t smem, cudaStream_t st)
+{
+    return a.equal_mass ? launch_adj_e<TM, ACC, true>(a, smem, st)
+                        : launch_adj_e<TM, ACC, false>(a, smem, st);
 }
 
 int launch_adj_f32(const FwdArgs& a, int precision, void* stream)
@@ -879,9 +889,9 @@ int adj_occupancy(int precision, int interp, int accum, int warps, int max_leaf,
     } else {
         smem = adj_f32_smem(precision, interp, table_n, warps, cap);
 #define PSR_PICK(TM, ACC) (variant != PSR_KERNEL_PACKED \
-                               ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, false> \
-                               : wide ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, true> \
-                                      : (const void*)p2p_adj_f32_kernel<TM, ACC, false, true>)
+                               ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, false, false> \
+                               : wide ? (const void*)p2p_adj_f32_kernel<TM, ACC, true, true, false> \
+                                      : (const void*)p2p_adj_f32_kernel<TM, ACC, false, true, false>)
         if (precision == PSR_FP32_EXACT)
             f = accum == PSR_ACC_FP64 ? PSR_PICK(TM_EXACT, PSR_ACC_FP64) : PSR_PICK(TM_EXACT, PSR_ACC_KAHAN32);
         else if (interp == PSR_LINEAR)

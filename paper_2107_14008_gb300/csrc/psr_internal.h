@@ -34,7 +34,8 @@ struct alignas(16) BoxDev {
     float g_acc;    // G / (2 r_s)^2: FP32 coordinate sums -> acceleration
     float g_adj;    // G / (8 r_s^3): adjoint position gradient factor
     float g_adjm;   // G / (4 r_s^2): adjoint mass gradient factor
-    float pad2, pad3;
+    float m_eq;     // the mass every particle of the box has (as FP32), 0 if they differ
+    float pad3;
 };
 static_assert(sizeof(BoxDev) == 96, "BoxDev layout");
 
@@ -107,6 +108,7 @@ struct Leaves {
     int64_t n_pairs = 0;
     bool has_pd = false;        // FP64 payload present in the workspace
     bool device_built = false;  // arrays were built on the device
+    bool equal_mass = false;    // in every box all particles share one mass (BoxDev::m_eq)
     bool has_far = false;       // pair list split into P2P (near) and M2L (far) entries
     double theta = 0.0;         //   multipole acceptance parameter of that split
     int64_t n_far = 0;          //   far entries
@@ -168,6 +170,7 @@ struct FwdArgs {
     int stage_cap;   // FP32 kernels: staged particles per warp
     int item_stride; // this launch takes schedule entries ticket * stride + offset
     int item_offset;
+    int equal_mass;  // every box has one particle mass: the FP32 kernels take it out of the sums
 };
 
 int launch_table(int table_n, int interp, double x_c, void* d_out, void* d_q_out, void* stream);

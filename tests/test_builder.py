@@ -227,6 +227,22 @@ def test_positions_outside_box_are_wrapped():
     np.testing.assert_array_equal(a1["pairs"], a0["pairs"])
 
 
+def test_equal_mass_flag():
+    """psr_info.equal_mass: 1 when every particle of each box has one mass
+    (also for mass = NULL, which means 1/n each), 0 as soon as one differs."""
+    b = synth.small(nside=8)
+    assert _build(b).info.equal_mass == 1
+    assert psr.Leaves.build(b.pos, None, b.L, b.r_s, b.r_c).info.equal_mass == 1
+    m = b.mass.copy()
+    m[17] *= 1.0 + 1e-12
+    assert psr.Leaves.build(b.pos, m, b.L, b.r_s, b.r_c).info.equal_mass == 0
+    c = synth.small(seed=7, nside=6)
+    both = [(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G), (c.pos, c.mass, c.L, c.r_s, c.r_c, c.G)]
+    assert psr.Leaves.build_batch(both).info.equal_mass == 1  # 1/512 and 1/216: one per box
+    both[1] = (c.pos, np.linspace(1.0, 2.0, c.n), c.L, c.r_s, c.r_c, c.G)
+    assert psr.Leaves.build_batch(both).info.equal_mass == 0
+
+
 def test_fp32_peak_rejects_bad_arguments_before_any_launch():
     with pytest.raises(capi.PsrError) as e:
         capi.psr_fp32_peak(0, 1 << 20, 16, 1, 0, 1000)

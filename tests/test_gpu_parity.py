@@ -278,17 +278,30 @@ def test_coincident_particles_give_finite_adjoint(kernel):
         assert rel_rms(gm, gm_ref) < tol, prec
 
 
-def test_deterministic_and_batch_equals_single_boxes():
-    boxes = [synth.small(nside=12), _clustered(n=3000), _small_box()]
+@pytest.mark.parametrize("equal", [False, True])
+def test_deterministic_and_batch_equals_single_boxes(equal):
+    """A batch gives each box the forces of that box alone, bit for bit, and
+    repeats them bit for bit: with per-particle masses (the general per-pair
+    form), and with one mass per box (every box takes the equal-mass path,
+    alone as in the batch)."""
+    small = synth.small(nside=12)
+    if equal:
+        boxes = [small, synth.small(seed=9, nside=10), synth.precision(nside=16, L=60.0, n_halos=4)]
+    else:
+        varied = synth.Box(pos=small.pos, mass=np.linspace(0.5, 1.5, small.n), L=small.L,
+                           n_pm=small.n_pm, r_s=small.r_s, r_c=small.r_c)
+        boxes = [varied, _clustered(n=3000), _small_box()]
     opts = psr.Options(precision=psr.PSR_FP32_TABLE)
     lv = psr.Leaves.build_batch([(b.pos, b.mass, b.L, b.r_s, b.r_c, b.G) for b in boxes],
                                 max_leaf=32).upload()
+    assert lv.info.equal_mass == int(equal)
     a1 = lv.forces(opts).cpu().numpy()
     a2 = lv.forces(opts).cpu().numpy()
     np.testing.assert_array_equal(a1, a2)
     off = 0
     for b in boxes:
-        single, _ = gpu_forces(b, opts, 32)
+        single, one = gpu_forces(b, opts, 32)
+        assert one.info.equal_mass == int(equal)
         np.testing.assert_array_equal(a1[off:off + b.n], single.astype(np.float32))
         off += b.n
 
@@ -732,4 +745,57 @@ def test_fp32_peak_probe_measures_a_positive_rate():
     with pytest.raises(capi.PsrError) as e:
         capi.psr_fp32_peak(sink.data_ptr(), used * 4 - 4, 64, 1, 0, 30000)
     assert e.value.code == capi.PSR_E_ARG
+
+
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+@pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
+@pytest.mark.parametrize("max_leaf", [32, 64])
+def test_equal_mass_path_matches_the_general_path(kernel, accum, max_leaf):
+    """With one mass for every particle (psr_info.equal_mass) the FP32
+    forward and adjoint kernels apply it once per target; the same positions
+    with one mass changed by a part in 10^12 take the general per-pair form.
+    Forces and both gradients agree to FP32 rounding, and the equal-mass
+    results match the oracle within the FP32 tolerances."""
+    b = _clustered()
+    m = np.full(b.n, 0.7)
+    m2 = m.copy()
+    m2[5] *= 1.0 + 1e-12
+    lv1 = psr.Leaves.build(b.pos, m, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
+    lv2 = psr.Leaves.build(b.pos, m2, b.L, b.r_s, b.r_c, b.G, max_leaf=max_leaf).upload()
+    assert lv1.info.equal_mass == 1 and lv2.info.equal_mass == 0
+    o = psr.Options(kernel=kernel, accum=accum)
+    a1 = lv1.forces(o).double().cpu().numpy()
+    a2 = lv2.forces(o).double().cpu().numpy()
+    lv1.check()
+    lv2.check()
+    assert rel_rms(a1, a2) < 1e-6
+    ref, _, _ = oracle.forces(b.pos % b.L, m, b.L, b.r_s, b.r_c, b.G)
+    assert rel_rms(a1, ref) < 2e-5
+    assert max_rel(a1, ref) < MAX_REL_FP32
+    cot = synth.cotangent(b.n, 9)
+    g1, h1 = lv1.adjoint(torch.tensor(cot), o)
+    g2, h2 = lv2.adjoint(torch.tensor(cot), o)
+    g1, h1 = g1.double().cpu().numpy(), h1.double().cpu().numpy()
+    g2, h2 = g2.double().cpu().numpy(), h2.double().cpu().numpy()
+    assert rel_rms(g1, g2) < 1e-6 and rel_rms(h1, h2) < 1e-6
+    gref, href = oracle.adjoint(b.pos % b.L, m, cot, b.L, b.r_s, b.r_c, b.G, cells=True)
+    assert rel_rms(g1, gref) < 2e-5 and rel_rms(h1, href) < 2e-5
+
+
+def test_equal_mass_flag_of_a_device_built_leaf_set():
+    """The GPU builder detects one mass for all particles as the host builder
+    does, and the forces of both leaf sets agree bit for bit."""
+    b = synth.small(nside=16)
+    pos = torch.tensor(b.pos, device="cuda")
+    for mass in (b.mass, np.linspace(0.5, 1.5, b.n)):
+        dv = psr.Leaves.device_build(pos, torch.tensor(mass, device="cuda"), b.L, b.r_s, b.r_c,
+                                     b.G, max_leaf=32)
+        hv = psr.Leaves.build(b.pos, mass, b.L, b.r_s, b.r_c, b.G, max_leaf=32).upload()
+        eq = int(np.all(mass == mass[0]))
+        assert dv.info.equal_mass == eq and hv.info.equal_mass == eq
+        o = psr.Options(precision=psr.PSR_FP32_TABLE)
+        assert torch.equal(dv.forces(o), hv.forces(o))
+        dv.check()
+    dv = psr.Leaves.device_build(pos, None, b.L, b.r_s, b.r_c, b.G, max_leaf=32)
+    assert dv.info.equal_mass == 1
 
