@@ -5,14 +5,16 @@
 // shared memory between two barriers; the Core loop over the staged
 // particles.  Pair arithmetic, tables and accumulation are those of the
 // warp-per-leaf kernels (leaf-local FP32 coordinates, exact leaf-centre
-// offsets, FP32 partial sums folded into FP64 or compensated FP32), so that
-// only the work mapping differs.  Blocks hold 32 threads, or 64 when a leaf
-// holds more than 32 particles.
+// offsets, FP32 partial sums folded into FP64 or compensated FP32, and with
+// one mass for all particles, as in the paper's Core function with its
+// single GM, the mass applied once per target), so that only the work
+// mapping differs.  Blocks hold 32 threads, or 64 when a leaf holds more
+// than 32 particles.
 #include "fwd_f32_common.cuh"
 
 namespace psr {
 
-template <int TM, int ACC, bool COUNT>
+template <int TM, int ACC, bool COUNT, bool EQM>
 __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
                     const float tt = TM == TM_LINEAR ? fma_sat(r2, rinv, soff)
                                                      : fmaf(r2, rinv, TM == TM_TAYLOR ? 0.0f : -0.5f);
                     const float Tv = eval_T1<TM>(tt, r2, rinv, tab_bias, nmax, x_c, xscale);
-                    const float w = p.w * Tv * rinv * rinv * rinv;
+                    const float w = EQM ? Tv * rinv * rinv * rinv : p.w * Tv * rinv * rinv * rinv;
                     fx = fmaf(w, dx, fx);
                     fy = fmaf(w, dy, fy);
                     fz = fmaf(w, dz, fz);
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(64) p2p_fwd_blk_kernel(const FwdArgs a)
         }
         if (act) {
             acc.fold(fx, fy, fz);
-            const float gout = bx.g_acc * sc * sc;
+            const float gout = bx.g_acc * sc * sc * (EQM ? bx.m_eq : 1.0f);
             float* out = reinterpret_cast<float*>(a.out) + 3LL * a.perm[li.x + t];
             if (ACC == PSR_ACC_FP64) {
                 out[0] = (float)(acc.x * (double)gout);
@@ -157,10 +159,10 @@ size_t blk_smem(int precision, int interp, int table_n, int threads)
     return ((tab + 15) & ~(size_t)15) + (size_t)threads * 16;
 }
 
-template <int TM, int ACC, bool COUNT>
+template <int TM, int ACC, bool COUNT, bool EQM>
 int launch_t(const FwdArgs& a, size_t smem, int threads, cudaStream_t st)
 {
-    auto k = p2p_fwd_blk_kernel<TM, ACC, COUNT>;
+    auto k = p2p_fwd_blk_kernel<TM, ACC, COUNT, EQM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -172,12 +174,13 @@ int launch_t(const FwdArgs& a, size_t smem, int threads, cudaStream_t st)
 template <int TM, int ACC>
 int launch_c(const FwdArgs& a, size_t smem, int threads, cudaStream_t st)
 {
-    return a.count_pairs ? launch_t<TM, ACC, true>(a, smem, threads, st)
-                         : launch_t<TM, ACC, false>(a, smem, threads, st);
+    return a.count_pairs  ? launch_t<TM, ACC, true, false>(a, smem, threads, st)
+           : a.equal_mass ? launch_t<TM, ACC, false, true>(a, smem, threads, st)
+                          : launch_t<TM, ACC, false, false>(a, smem, threads, st);
 }
 
 template <int TM, int ACC>
-const void* ptr_c() { return (const void*)p2p_fwd_blk_kernel<TM, ACC, false>; }
+const void* ptr_c() { return (const void*)p2p_fwd_blk_kernel<TM, ACC, false, false>; }
 
 int pick_tm(int precision, int interp)
 {

@@ -747,7 +747,8 @@ def test_fp32_peak_probe_measures_a_positive_rate():
     assert e.value.code == capi.PSR_E_ARG
 
 
-@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED])
+@pytest.mark.parametrize("kernel", [psr.PSR_KERNEL_SCALAR, psr.PSR_KERNEL_PACKED,
+                                    psr.PSR_KERNEL_PAPER])
 @pytest.mark.parametrize("accum", [psr.PSR_ACC_FP64, psr.PSR_ACC_KAHAN32])
 @pytest.mark.parametrize("max_leaf", [32, 64])
 def test_equal_mass_path_matches_the_general_path(kernel, accum, max_leaf):
