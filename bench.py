@@ -70,6 +70,8 @@ def parse():
                         "takes a tenth of them)")
     p.add_argument("--no-variants", dest="variants", action="store_false",
                    help="skip the precision study (one launch per T variant)")
+    p.add_argument("--autograd-steps", type=int, default=5,
+                   help="timed forward + backward steps through psr.forces (torch autograd)")
     p.add_argument("--peak-launches", type=int, default=5,
                    help="launches of the FP32 FMA-rate microbenchmark (psr_fp32_peak); 0 skips it")
     p.add_argument("--peak-iters", type=int, default=65536,
@@ -837,6 +839,38 @@ def run_psr(args):
                 "targets": int(tg.size),
                 "dL_dx": float(np.sqrt(np.sum(dg * dg) / np.sum(gref * gref))),
                 "dL_dm": float(np.sqrt(np.sum(dm * dm) / np.sum(mref * mref)))}
+
+        # the same forward + backward through the differentiable entry point
+        # (psr.forces, a torch.autograd.Function): GPU leaf build from the
+        # CUDA positions, forward kernel, adjoint kernel, every step
+        if args.autograd_steps > 0:
+            pos_t = torch.tensor(b.pos, dtype=torch.float64, device=dev, requires_grad=True)
+            mass_t = torch.tensor(b.mass, dtype=torch.float64, device=dev, requires_grad=True)
+            cot64 = cot.double()
+
+            def ag_step():
+                pos_t.grad = mass_t.grad = None
+                a_ = psr.forces(pos_t, mass_t, b.L, b.r_s, b.r_c, b.G, opts, b.max_leaf)
+                a_.backward(cot64)
+
+            ag_step()  # warm-up (allocator)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for k in range(args.autograd_steps):
+                ag_step()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms_ag = s0.elapsed_time(s1) / args.autograd_steps
+            dg = pos_t.grad.float() - gp
+            adj["autograd"] = {
+                "ms_per_step": ms_ag, "steps": args.autograd_steps,
+                "includes": "psr.forces on CUDA tensors: GPU leaf build, forward kernel; "
+                            "backward(): adjoint kernel (L2 not flushed between steps)",
+                "resident_forward_plus_adjoint_ms": mean_ms + ms_a,
+                "grad_pos_rel_rms_vs_resident_adjoint":
+                    float(torch.sqrt((dg * dg).sum() / (gp * gp).sum()))}
+            del pos_t, mass_t
 
     # the precision study: every T variant and accumulation, one launch each
     variants = []
